@@ -1,0 +1,266 @@
+"""Pins of the oracle's FR numerics: textbook operator identities, the DG lift identity, the
+SSP-RK3 stability polynomial, transfer identities, the vortex as a steady Euler solution,
+freestream preservation and discrete conservation on nonconforming trees, and p+1 convergence
+(no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_06744_gb300 import workloads as W
+
+
+def _gl_closed_form(n):
+    if n == 2:
+        return [-1 / math.sqrt(3), 1 / math.sqrt(3)]
+    if n == 3:
+        return [-math.sqrt(3 / 5), 0.0, math.sqrt(3 / 5)]
+    if n == 4:
+        a = math.sqrt(3 / 7 - 2 / 7 * math.sqrt(6 / 5))
+        b = math.sqrt(3 / 7 + 2 / 7 * math.sqrt(6 / 5))
+        return [-b, -a, a, b]
+    if n == 5:
+        a = math.sqrt(5 - 2 * math.sqrt(10 / 7)) / 3
+        b = math.sqrt(5 + 2 * math.sqrt(10 / 7)) / 3
+        return [-b, -a, 0.0, a, b]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_operators(p):
+    n = p + 1
+    o = O.operators(p)
+    assert np.allclose(o["x"], _gl_closed_form(n), atol=1e-15, rtol=0)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    assert np.allclose(o["w"], wr, atol=1e-14, rtol=0)
+    assert abs(o["w"].sum() - 2.0) < 1e-14
+    # differentiation matrix: exact on monomials of degree <= p, rows sum to zero
+    for k in range(n):
+        fx = o["x"] ** k
+        dfx = k * o["x"] ** (k - 1) if k else np.zeros(n)
+        assert np.allclose(o["D"] @ fx, dfx, atol=1e-13)
+    # boundary interpolation reproduces polynomials of degree <= p
+    for k in range(n):
+        assert abs(o["lm"] @ o["x"] ** k - (-1.0) ** k) < 1e-13
+        assert abs(o["lp"] @ o["x"] ** k - 1.0) < 1e-13
+    # correction function: g_L(-1) = 1, g_L(1) = 0 (Sec. 2.1)
+    assert abs(O.correction_gL(p, -1.0) - 1.0) < 1e-15
+    assert abs(O.correction_gL(p, 1.0)) < 1e-15
+    # DG lift identity (Huynh): the Radau correction recovers nodal DG,
+    # g_L'(x_i) = -l_i(-1)/w_i and g_R'(x_i) = l_i(1)/w_i
+    assert np.allclose(o["gL"], -o["lm"] / o["w"], atol=1e-12)
+    assert np.allclose(o["gR"], o["lp"] / o["w"], atol=1e-12)
+
+
+def test_rk3_stability_polynomial():
+    for z in (-0.3, -1.0, 0.5, -2.4):
+        got = O.rk3_scalar(z, 1.0, 1.0)
+        assert abs(got - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15
+
+
+def _poly_field(dim, p, xs, coeff_seed):
+    """A random polynomial of degree <= p per axis, sampled at the tensor points xs (1D)."""
+    c = W.random_uniform((p + 1) ** dim, coeff_seed) - 0.5
+    n = p + 1
+    pts = np.array(np.meshgrid(*([xs] * dim), indexing="ij")).reshape(dim, -1)[::-1]
+    # meshgrid 'ij' then reverse -> pts[a] varies with x fastest in the flattened index
+
+    def f(X):
+        val = 0.0
+        for idx in range(n ** dim):
+            t, term = idx, c[idx]
+            for a in range(dim):
+                term *= X[a] ** (t % n)
+                t //= n
+            val += term
+        return val
+
+    return f
+
+
+@pytest.mark.parametrize("dim,p", [(2, 1), (2, 2), (2, 3), (3, 2), (3, 3)])
+def test_transfer_identities(dim, p):
+    o = O.operators(p)
+    n = p + 1
+    N = n ** dim
+    xs = o["x"]
+    idx = np.arange(N)
+    coords = [xs[(idx // n ** a) % n] for a in range(dim)]
+    f = _poly_field(dim, p, xs, 5 + dim * 10 + p)
+    parent = np.array([[f([coords[a][i] for a in range(dim)]) for i in range(N)]] * 2)
+    parent[1] *= 2.0
+    kids = []
+    for c in range(1 << dim):
+        k = O.prolong(dim, p, parent, c)
+        # refinement reproduces the degree-p polynomial exactly at the child points
+        want = [f([(coords[a][i] + 2 * ((c >> a) & 1) - 1) / 2 for a in range(dim)]) for i in range(N)]
+        assert np.allclose(k[0], want, atol=1e-13)
+        kids.append(k)
+    kids = np.array(kids)
+    back = O.restrict(dim, p, kids)
+    # restriction after refinement is the identity
+    assert np.allclose(back, parent, atol=1e-13)
+    # restriction conserves the integral sum_i w_i |J| u_i for arbitrary child data
+    W1 = np.ones(N)
+    for a in range(dim):
+        W1 = W1 * o["w"][(idx // n ** a) % n]
+    rnd = (W.random_uniform(kids.size, 99).reshape(kids.shape) - 0.5)
+    pr = O.restrict(dim, p, rnd)
+    lhs = (pr * W1).sum(axis=-1)
+    rhs = (rnd * W1).sum(axis=-1).sum(axis=0) / 2 ** dim
+    assert np.allclose(lhs, rhs, atol=1e-14)
+
+
+def test_vortex_is_steady_euler_solution():
+    # In the frame moving with the freestream the isentropic vortex is a steady Euler solution:
+    # isentropic (p = rho^gamma for rho_inf = p_inf = 1) and in radial balance dp/dr = rho v_t^2 / r.
+    cfg = W.config("vortex2d_p2_small")
+    cfg["uinf"] = (0.0, 0.0, 0.0)
+    g = cfg["gamma"]
+    r = np.linspace(0.2, 3.0, 15)
+    h = 1e-5
+    pts = np.array([[5.0 + rr, 5.0, 0.0] for rr in r])
+    ptsp = np.array([[5.0 + rr + h, 5.0, 0.0] for rr in r])
+    ptsm = np.array([[5.0 + rr - h, 5.0, 0.0] for rr in r])
+
+    def pres(q):
+        return (g - 1) * (q[:, 3] - 0.5 * (q[:, 1] ** 2 + q[:, 2] ** 2) / q[:, 0])
+
+    q, qp, qm = O.exact(cfg, 0.0, pts), O.exact(cfg, 0.0, ptsp), O.exact(cfg, 0.0, ptsm)
+    rho, p = q[:, 0], pres(q)
+    assert np.allclose(p, rho ** g, rtol=1e-13)
+    vt = q[:, 2] / rho  # on the +x ray the tangential velocity is v
+    dpdr = (pres(qp) - pres(qm)) / (2 * h)
+    assert np.allclose(dpdr, rho * vt ** 2 / r, rtol=1e-6)
+    # centre value, far field, and advection by the freestream
+    cfg2 = W.config("vortex2d_p2_small")
+    qc = O.exact(cfg2, 0.0, np.array([[5.0, 5.0, 0.0]]))
+    dT = -(g - 1) * 25 / (8 * g * math.pi ** 2) * math.e
+    assert abs(qc[0, 0] - (1 + dT) ** (1 / (g - 1))) < 1e-14
+    qf = O.exact(cfg2, 0.0, np.array([[0.0, 0.0, 0.0]]))
+    assert abs(qf[0, 0] - 1.0) < 1e-9
+    x0 = np.array([[5.3, 4.1, 0.0]])
+    q0 = O.exact(cfg2, 0.0, x0)
+    q1 = O.exact(cfg2, 1.7, x0 + np.array([[1.7, 1.7, 0.0]]))
+    assert np.allclose(q0, q1, atol=1e-13)
+
+
+def _random_nonconforming_mesh(dim, p, Dbase, Dmax, seed, psplit):
+    cfg = W.config("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube")
+    cfg.update(dim=dim, p=p, Dbase=Dbase, Dmax=Dmax, init_passes=0, indicator=2, dt=1e-3)
+    m = O.OracleMesh(cfg)
+    for k in range(50):  # first seed of the sequence whose tree has hanging faces
+        boxes = W.random_tree_boxes(dim, Dbase, Dmax, seed=seed + 1000 * k, p_split=psplit)
+        keys = O.balance(dim, Dmax, np.sort(O.morton_encode(dim, Dmax, boxes)))
+        if (O.conn(dim, Dmax, keys)[1] == 2).any():
+            break
+    return cfg, m, keys
+
+
+def _depths(dim, Dmax, keys):
+    return O.morton_decode(dim, Dmax, keys)[:, 0]
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax,seed", [(2, 1, 2, 5, 1), (2, 2, 2, 5, 2), (2, 3, 2, 5, 3),
+                                                   (3, 1, 1, 3, 4), (3, 2, 1, 3, 5)])
+def test_freestream_preservation(dim, p, Dbase, Dmax, seed):
+    cfg, m, keys = _random_nonconforming_mesh(dim, p, Dbase, Dmax, seed, 0.35)
+    _, ft, _ = O.conn(dim, Dmax, keys)
+    assert (ft == 1).any() and (ft == 2).any(), "mesh must have hanging faces"
+    M, nv, N = keys.shape[0], dim + 2, (p + 1) ** dim
+    q = np.array([1.3, 1.3 * 0.7, -1.3 * 0.4, 0.0, 0.0][:nv])
+    if dim == 3:
+        q[3] = 1.3 * 0.25
+    q[-1] = 2.0 / (cfg["gamma"] - 1) + 0.5 * (q[1:1 + dim] ** 2).sum() / q[0]
+    u = np.broadcast_to(q[None, :, None], (M, nv, N)).copy()
+    m.set_state(keys, u)
+    R = m.rhs()
+    assert np.abs(R).max() < 1e-12
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax,seed", [(2, 2, 2, 5, 6), (2, 3, 2, 6, 7), (3, 2, 1, 3, 8),
+                                                   (3, 3, 1, 3, 9)])
+def test_discrete_conservation(dim, p, Dbase, Dmax, seed):
+    # sum_e sum_i w_i |J_e| R_{e,i} = 0 on a nonconforming periodic mesh with a random state:
+    # the mortar back-projection is an L2 projection (Sec. 4.3)
+    cfg, m, keys = _random_nonconforming_mesh(dim, p, Dbase, Dmax, seed, 0.35)
+    M, nv, N, n = keys.shape[0], dim + 2, (p + 1) ** dim, p + 1
+    rnd = W.random_uniform(M * nv * N, seed + 40).reshape(M, nv, N) - 0.5
+    u = np.zeros((M, nv, N))
+    u[:, 0] = 1.0 + 0.2 * rnd[:, 0]
+    for b in range(dim):
+        u[:, 1 + b] = 0.3 * rnd[:, 1 + b]
+    u[:, -1] = 2.5 + 0.2 * rnd[:, -1]
+    m.set_state(keys, u)
+    R = m.rhs()
+    o = O.operators(p)
+    idx = np.arange(N)
+    Wt = np.ones(N)
+    for a in range(dim):
+        Wt = Wt * o["w"][(idx // n ** a) % n]
+    h = cfg["L"] / 2.0 ** _depths(dim, Dmax, keys)
+    J = (h / 2) ** dim
+    tot = np.einsum("evi,i,e->v", R, Wt, J)
+    scale = np.einsum("evi,i,e->v", np.abs(R), Wt, J)
+    assert np.all(np.abs(tot) < 1e-13 * scale.max() + 1e-14), (tot, scale)
+
+
+def test_3d_tube_reduces_to_2d():
+    # a z-uniform 3D mesh carrying the vortex tube must reproduce the 2D residual in every layer
+    c2 = W.config("vortex2d_p2_small")
+    c2.update(Dbase=3, Dmax=3, init_passes=0, indicator=2)
+    c3 = dict(c2, dim=3)
+    m2, m3 = O.OracleMesh(c2), O.OracleMesh(c3)
+    R2, R3 = m2.rhs(), m3.rhs()
+    k3 = m3.leaves()
+    b3 = O.morton_decode(3, 3, k3)
+    k2 = m2.leaves()
+    b2 = O.morton_decode(2, 3, k2)
+    pos2 = {(x, y): i for i, (_, x, y, _) in enumerate(b2)}
+    n, N2 = 3, 9
+    for e in range(0, len(k3), 7):
+        _, x, y, z = b3[e]
+        e2 = pos2[(x, y)]
+        for iz in range(n):
+            layer = R3[e, :, iz * N2:(iz + 1) * N2]
+            assert np.allclose(layer[[0, 1, 2, 4]], R2[e2], atol=1e-12)
+            assert np.abs(layer[3]).max() < 1e-12
+
+
+def _uniform_error(p, D, t_end, dt, L=20.0):
+    cfg = W.config("vortex2d_p2_small")
+    cfg.update(p=p, L=L, Dbase=D, Dmax=D, init_passes=0, indicator=2, dt=dt,
+               vort=np.array([[L / 2, L / 2, 5.0, 1.0]]))
+    m = O.OracleMesh(cfg)
+    m.step(int(round(t_end / dt)))
+    return m.norms()["l2_rho"]
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_convergence_order(p):
+    # order ~ p+1 on uniform meshes for the advected vortex (Sec. 5.2, Table of uniform meshes)
+    dt = 0.01 if p < 3 else 0.005
+    e1 = _uniform_error(p, 4, 0.5, dt)
+    e2 = _uniform_error(p, 5, 0.5, dt)
+    order = math.log(e1 / e2) / math.log(2.0)
+    assert order > p + 0.5, (e1, e2, order)
+
+
+def test_adaptive_matches_uniform_error():
+    # Sec. 5.2: adaptive and uniform meshes with the same finest spacing give L2 density errors
+    # that differ only trivially.  Analytic-centre criterion with the paper's radii 5 and 6.
+    L = 20.0
+
+    def run(Dbase, Dmax, passes, ind):
+        cfg = W.config("vortex2d_p2_small")
+        cfg.update(p=2, L=L, Dbase=Dbase, Dmax=Dmax, init_passes=passes, indicator=ind, dt=0.01,
+                   th_refine=5.0, th_coarsen=6.0, adapt_every=10,
+                   vort=np.array([[L / 2, L / 2, 5.0, 1.0]]))
+        m = O.OracleMesh(cfg)
+        m.run(50)
+        return m.norms()["l2_rho"], m.M
+
+    eu, Mu = run(5, 5, 0, 2)
+    ea, Ma = run(3, 5, -1, 1)
+    assert Ma < Mu / 2
+    assert abs(ea - eu) < 0.01 * eu, (ea, eu)
