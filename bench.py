@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of one adaptive FR cycle on the 2D p=3 vortex workload (periodic [0,40]^2, base level
+5, max level 9, density-gradient indicator), FP64.
+
+One bench step = one pass of the whole hot path: `adapt_every` (10) SSP-RK3 time steps -- each
+stage an interface kernel (Rusanov, mortar projection) and an element kernel (corrected-flux
+divergence, RK combination, traces) -- followed by one adaptation (indicator, refine/coarsen edit,
+2:1 balance, mapping, transfer, connectivity).  K timed steps after W warm-up steps; L2 is flushed
+between steps (a 512 MB write outside the timed events).
+
+value  = DOF-updates/s = sum over time steps of M*N*nv / device time of the K cycles.
+e2e    = the same metric through the public API with host buffers: fr_set_state from pinned host
+         arrays, the cycle, fr_get_leaves + fr_get_state back to host, every step.
+--impl reference times the CPU oracle (single thread) on the same workload, one cycle per step.
+With --gpus N > 1 every rank runs an independent replica (the method does not shard here).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "adaptive FR DOF-updates/s at fixed vortex L2 error; adaptation % of walltime"
+UNIT = "DOF-updates/s"
+WORKLOAD = "vortex2d_p3"
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12  # 2 DFMA/clk/SM x 152 SMs x 2.07 GHz = 1.259 TFLOP/s
+
+
+def flops_per_point_stage(dim, p):
+    """Algorithmic FP64 flops of the element kernel per solution point (sum-factorised form):
+    primitives, Euler fluxes, folded derivative+correction, RK combination, traces of the result.
+    A divide or square root counts as one flop."""
+    n, nv = p + 1, dim + 2
+    prim = 3 * dim + 1 + 3
+    flux = dim * (dim + 3)
+    deriv = dim * nv * (2 * n + 3)
+    rk = 6 * nv
+    traces = 4 * dim * nv
+    return prim + flux + deriv + rk + traces
+
+
+def bytes_per_point_stage(dim, p):
+    """Algorithmic DRAM bytes of the element kernel per solution point: read u_s, read u^n, write
+    the result, read the common fluxes and write the traces (2*dim*nv/n values each)."""
+    n, nv = p + 1, dim + 2
+    return 8 * (3 * nv + 2 * (2 * dim * nv / n))
+
+
+def _clock_sampler_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        fh = open(path, "w")
+        return subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                 "-lms", "200"], stdout=fh, stderr=subprocess.DEVNULL), fh
+    except Exception:
+        return None, None
+
+
+def _clock_sampler_stop(proc, fh, path, device_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    fh.close()
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            if int(parts[0]) != device_index:
+                continue
+            sm.append(float(parts[1]))
+            mx = max(mx, float(parts[2]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, parts[5:9]):
+            if val.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def _cpu_baseline(cfg, budget_s=12.0):
+    """The oracle as it stands, single-threaded, on a bounded sample: whole cycles of the same
+    workload (10 steps + 1 adaptation) until the time budget is used."""
+    import oracle as O
+    o = O.OracleMesh(cfg)
+    N, nv = (cfg["p"] + 1) ** cfg["dim"], cfg["dim"] + 2
+    dof, cycles = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        M = o.M
+        o.step(cfg["adapt_every"])
+        o.adapt()
+        dof += cfg["adapt_every"] * M * N * nv
+        cycles += 1
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    return {"value": dof / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d cycles (10 SSP-RK3 steps + 1 adaptation each) of %s from its initial "
+                      "mesh, %.1f s" % (cycles, WORKLOAD, el)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2306_06744_gb300 import workloads as W
+    cfg = W.config(WORKLOAD)
+    o = O.OracleMesh(cfg)
+    N, nv = (cfg["p"] + 1) ** cfg["dim"], cfg["dim"] + 2
+    for _ in range(args.warmup):
+        o.step(cfg["adapt_every"])
+        o.adapt()
+    dof, t_steps, t_adapt = 0, 0.0, 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        M = o.M
+        a = time.perf_counter()
+        o.step(cfg["adapt_every"])
+        b = time.perf_counter()
+        o.adapt()
+        c = time.perf_counter()
+        t_steps += b - a
+        t_adapt += c - b
+        dof += cfg["adapt_every"] * M * N * nv
+    el = time.perf_counter() - t0
+    value = dof / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": 2, "p": 3, "domain": "[0,40]^2", "Dbase": 5,
+                       "Dmax": 9, "adapt_every": 10, "l2": "n/a (CPU)"},
+            "adaptation_pct": 100.0 * t_adapt / (t_steps + t_adapt),
+            "l2_rho": o.norms()["l2_rho"], "M_final": o.M,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d cycles of %s after %d warm-up cycles" %
+                                       (args.steps, WORKLOAD, args.warmup)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def _traffic_from_profiles(kernel):
+    """Per-launch DRAM bytes of `kernel` recorded in profiles/, if the recorded source hash still
+    matches the kernel source (otherwise the counters are stale: None)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2306_06744_gb300", "csrc", "fr_solver.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith(".md"):
+            continue
+        vals = {}
+        for line in open(os.path.join(pdir, fn)):
+            if line.startswith("bench-key:"):
+                parts = line.split()
+                if len(parts) >= 4:
+                    vals[parts[1]] = parts[2:]
+        rec = vals.get(kernel)
+        if rec and rec[1] == h:
+            try:
+                return float(rec[0])
+            except ValueError:
+                return None
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_06744_gb300 import fr
+    from paper_2306_06744_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cfg = W.config(WORKLOAD)
+    dim, p = cfg["dim"], cfg["p"]
+    N, nv = (p + 1) ** dim, dim + 2
+    ae = cfg["adapt_every"]
+    stream = torch.cuda.current_stream()
+    mesh = fr.Mesh(cfg, stream=stream)
+    for _ in range(args.warmup):
+        mesh.step(ae)
+        mesh.adapt()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    Ms = []
+    clk_path = os.path.join(tempfile.gettempdir(), "fr_bench_clocks_%d.csv" % os.getpid())
+    proc, fh = _clock_sampler_start(clk_path)
+    time.sleep(0.3)
+    mesh.profile_enable(True)
+    launches0 = fr.kernel_launches()
+    barrier()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        Ms.append(mesh.M)
+        e0, e1, e2 = evs[k]
+        e0.record(stream)
+        mesh.step(ae)
+        e1.record(stream)
+        mesh.adapt()
+        e2.record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = fr.kernel_launches() - launches0
+    prof = mesh.profile_read()
+    mesh.profile_enable(False)
+    clocks = _clock_sampler_stop(proc, fh, clk_path, local)
+    t_step = sum(a.elapsed_time(b) for a, b, _ in evs) / 1e3
+    t_adapt = sum(b.elapsed_time(c) for _, b, c in evs) / 1e3
+    t_tot = t_step + t_adapt
+    if world > 1:
+        tt = torch.tensor([t_tot], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_tot = float(tt.item())
+    dof_rank = sum(ae * m * N * nv for m in Ms)
+    value = world * dof_rank / t_tot
+    norms = mesh.norms()
+
+    # element-kernel roofline (FP64: bound by the FP64 pipe)
+    st_s = prof["stage_ms"] / 1e3
+    stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    flops = prof["stage_points"] * flops_per_point_stage(dim, p)
+    nbytes = prof["stage_points"] * bytes_per_point_stage(dim, p)
+    achieved_tflops = flops / st_s / 1e12
+    achieved_gbs = nbytes / st_s / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    traffic = _traffic_from_profiles("k_stage")
+    roofline = {"kernel": "k_stage<2,4> (element stage)", "bound": "alu",
+                "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (recipe unit counts "
+                               "and clocks)",
+                "avg_launch_ms": stage_avg_ms,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_peak, "peak_source": "measured" if peaks else "fallback"},
+                "share_of_step_time": (prof["stage_ms"] / 1e3) / t_step if t_step else None,
+                "face_kernel_share": (prof["face_ms"] / 1e3) / t_step if t_step else None}
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        keys_h = torch.empty(0)
+        dof_e, t_e, bi, bo = 0, 0.0, 0, 0
+        for k in range(args.e2e_steps + 1):
+            keys = mesh.leaves()
+            u = mesh.state()
+            kp = torch.from_numpy(keys.view(np.int64)).pin_memory()
+            up = torch.from_numpy(u).pin_memory()
+            kn, un_ = kp.numpy().view(np.uint64), up.numpy()
+            torch.cuda.synchronize()
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            mesh.set_state(kn, un_)
+            M0 = mesh.M
+            mesh.step(ae)
+            mesh.adapt()
+            k2 = mesh.leaves()
+            u2 = mesh.state()
+            b = time.perf_counter()
+            if k == 0:
+                continue  # first pass warms the pinned-buffer path
+            dof_e += ae * M0 * N * nv
+            t_e += b - a
+            bi += kn.nbytes + un_.nbytes
+            bo += k2.nbytes + u2.nbytes
+        e2e = {"value": world * dof_e / t_e, "unit": UNIT,
+               "h2d_bytes_per_step": bi // args.e2e_steps, "d2h_bytes_per_step": bo // args.e2e_steps}
+        del keys_h
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(cfg)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": dim, "p": p, "domain": "[0,40]^2",
+                       "Dbase": cfg["Dbase"], "Dmax": cfg["Dmax"], "adapt_every": ae,
+                       "time_steps_per_step": ae, "indicator": "density gradient 1e-8/2.5e-9",
+                       "l2": "flushed between steps (512 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "adaptation_pct": 100.0 * t_adapt / (t_step + t_adapt),
+            "l2_rho": norms["l2_rho"], "t_final": norms["t"], "M_final": mesh.M,
+            "M_mean": sum(Ms) / len(Ms), "wall_s": wall,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches}
+    if rank == 0:
+        print(json.dumps(line))
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

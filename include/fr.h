@@ -1,0 +1,209 @@
+/*
+ * fr.h -- C ABI of the GB300 (sm_103a) library for h-adaptive flux reconstruction (FR) of the
+ * compressible Euler equations on Morton-ordered linear quadtrees (2D) and octrees (3D), after
+ * Wang, Witherden & Jameson, "An efficient GPU-based h-adaptation framework via linear trees for
+ * the flux reconstruction method" (arXiv 2306.06744).
+ *
+ * Everything a call computes runs in this library's CUDA kernels on the caller's stream.
+ * The library owns every device buffer of a mesh.  Host arrays passed in or out are owned by
+ * the caller and are read or written before the call returns (the call synchronises its stream
+ * for them).  Calls on one mesh are not thread-safe; different meshes are independent.
+ *
+ * Canonical layouts (identical for input and output):
+ *   key   : uint64 Morton ID (Sec. 2.2, Algorithm 1): the anchor's interleaved coordinate bits at
+ *           the octant's depth D, most significant level first and, inside a level, z above y
+ *           above x; then dim*(Dmax-D) zero bits; then D in m_b = ceil(log2(Dmax+1)) bits.
+ *           Anchors count cells of the finest level Dmax.  Sorted ascending, ancestors sort
+ *           before descendants and a first child is its parent's key plus one (Sec. 3.2).
+ *   box   : int32[4] = (depth, x, y, z), anchor in finest-level cells (z = 0 in 2D).
+ *   u     : double[M][nv][N], nv = dim+2 conserved variables (rho, rho*u, rho*v, [rho*w], E),
+ *           N = (p+1)^dim Gauss-Legendre solution points, point i = ix + n*iy + n*n*iz.
+ *   faces : f = 2*axis + side (side 0 = minus face); the matching face of a neighbour is f^1.
+ *   conn  : per element and face (int32 nbr, int8 ftype, int8 slot): ftype 0 conforming (slot
+ *           -1); 1 = this element is the fine side of a 2:1 hanging face, nbr is the coarse
+ *           element and slot its position on the coarse face (child bits along the in-face axes,
+ *           lower axis least significant, Sec. 3.3); 2 = this element is the coarse side, nbr is
+ *           the slot-0 fine element (slot 0).
+ *
+ * Errors: every int-returning call returns 0 on success or one of the negative FR_E* codes; the
+ * message is available from fr_last_error(mesh) (or fr_last_error(NULL) for calls without a
+ * mesh).  No call traps or aborts on bad input.
+ */
+#ifndef FR_GB300_H
+#define FR_GB300_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FR_OK 0
+#define FR_EINVAL (-1)    /* bad argument, layout or configuration                        */
+#define FR_ENOMEM (-2)    /* device allocation failed                                       */
+#define FR_EOVERFLOW (-3) /* caller capacity too small (required size written back)        */
+#define FR_ETIMEOUT (-4)  /* a bounded device wait gave up (reserved; no kernel waits today) */
+#define FR_ECUDA (-5)     /* CUDA runtime error                                             */
+
+typedef struct fr_mesh fr_mesh;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a device
+   pointer usable on `stream`, or NULL on failure; free releases it in stream order.  With a NULL
+   allocator the library uses cudaMallocAsync / cudaFreeAsync on the mesh's stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} fr_allocator;
+
+/* Problem set-up (Sec. 2.1 and Sec. 5.2).  All fields are read at fr_mesh_init only. */
+typedef struct {
+  int32_t dim, p;          /* dim 2 or 3; polynomial degree p in 1..4                             */
+  double L;                /* periodic domain [0,L]^dim                                           */
+  int32_t Dbase, Dmax;     /* coarsest depth (uniform start, coarsening limit) and finest depth   */
+  double gamma;            /* ratio of specific heats                                             */
+  int32_t nvort;           /* number of vortices (>= 0)                                           */
+  const double* vort;      /* host [nvort][4]: x centre, y centre, strength beta, core radius     */
+  double uinf[3];          /* freestream velocity (the vortices move with it)                     */
+  double rho_inf, p_inf;   /* freestream density and pressure                                     */
+  double cfl, dt;          /* dt > 0 fixes the time step; otherwise dt = cfl*h(Dmax)/((2p+1)*smax)
+                              with smax the largest |v|+c of the initial state                    */
+  int32_t adapt_every;     /* fr_run adapts after every adapt_every steps (0: never)              */
+  int32_t indicator;       /* 0: density gradient eta = h*max|grad rho| (refine if eta >
+                              th_refine, coarsen if eta < th_coarsen); 1: analytic centre of
+                              Sec. 5.2 (th_refine, th_coarsen are the radii 5 and 6 of the paper);
+                              2: external flags only                                              */
+  double th_refine, th_coarsen;
+  int32_t precision;       /* 0: FP64 everywhere (the only form implemented)                      */
+  int32_t init_passes;     /* < 0: Dmax-Dbase passes of {closed-form state, flags, adaptation}    */
+} fr_config;
+
+typedef struct {
+  double t, l2_rho;     /* time and L2 norm of the density error against the closed form (Sec. 5.2) */
+  double integral[5];   /* domain integral of each conserved variable (GL quadrature x |J|)        */
+  double min_rho, min_p;
+  int64_t M;
+} fr_norms_out;
+
+typedef struct {
+  int64_t M_old, M_new;
+  int64_t n_refined, n_coarsened; /* leaves flagged and honoured                               */
+  int32_t balance_passes;         /* depth passes of the 2:1 balance that split something      */
+  double ms_tree, ms_transfer, ms_conn; /* device time of the three parts (Sec. 5.2 breakdown)  */
+} fr_adapt_stats;
+
+typedef struct {
+  int64_t steps;
+  int64_t dof_updates; /* sum over steps of M*N*nv                                             */
+  double ms;           /* device time of the steps                                             */
+} fr_step_stats;
+
+typedef struct {
+  double t, dt;
+  int64_t M, step;
+  int32_t dim, p, nv, N;
+  int64_t n_conforming, n_hanging; /* face lists of the current mesh                          */
+} fr_info;
+
+/* ---------------------------------------------------------------------------------------------
+ * Mesh-level calls
+ * ------------------------------------------------------------------------------------------- */
+
+/* Builds the initial mesh: uniform at Dbase, then init_passes of {closed-form vortex state
+   (Sec. 5.2) at the solution points, indicator flags, fr_adapt}; the state is the closed form on
+   the final tree.  `stream` is a cudaStream_t (NULL = legacy default stream).  `alloc` may be
+   NULL.  On success *out owns all device memory of the mesh.  FR_EINVAL for dim/p/Dbase/Dmax out
+   of range (dim*Dmax + m_b must fit in 63 bits). */
+int fr_mesh_init(const fr_config* cfg, const fr_allocator* alloc, void* stream, fr_mesh** out);
+
+/* Releases every buffer of the mesh (stream-ordered).  NULL is ignored. */
+void fr_mesh_free(fr_mesh* m);
+
+/* nsteps explicit SSP-RK3 steps (Eq. rk3) with the fixed dt: per stage one interface kernel
+   (Rusanov flux on conforming faces, mortar projection at hanging faces, Sec. 4.3) and one
+   element kernel (corrected-flux divergence, Sec. 2.1, and the Runge-Kutta combination).
+   stats may be NULL; when given, the call synchronises to time the steps. */
+int fr_step(fr_mesh* m, int nsteps, fr_step_stats* stats);
+
+/* nsteps steps with fr_adapt(m, NULL, ...) after every adapt_every-th step (by step count). */
+int fr_run(fr_mesh* m, int nsteps, fr_step_stats* step_stats, fr_adapt_stats* adapt_stats);
+
+/* One adaptation (Sec. 4.1 procedure, then 2:1 balance, old->new mapping, solution transfer
+   Sec. 4.2, connectivity Sec. 3.3).  flags: device int8[M] in {-1,0,1} borrowed for the call, or
+   NULL to evaluate the configured indicator.  Refinement at Dmax and coarsening at Dbase are
+   ignored; a leaf changes at most one level before balancing.  stats may be NULL. */
+int fr_adapt(fr_mesh* m, const int8_t* dev_flags, fr_adapt_stats* stats);
+
+/* Indicator flags of the current state (not applied).  host flags int8[M], eta double[M] (may be
+   NULL).  cap = capacity in elements; FR_EOVERFLOW if cap < M. */
+int fr_flags(fr_mesh* m, int8_t* host_flags, double* host_eta, int64_t cap);
+
+/* Right-hand side R(u) = -div F of the current state into host double[M][nv][N]. */
+int fr_rhs(fr_mesh* m, double* host_R, int64_t cap);
+
+/* Norms of the current state (deterministic FP64 reductions). */
+int fr_norms(fr_mesh* m, fr_norms_out* out);
+
+/* Copies out the sorted leaves; host_keys may be NULL to query M only. */
+int fr_get_leaves(fr_mesh* m, uint64_t* host_keys, int64_t cap, int64_t* M);
+int fr_get_state(fr_mesh* m, double* host_u, int64_t cap);
+/* Replaces tree and state (keys must form a complete, sorted, 2:1-balanced linear tree with
+   depths in [Dbase, Dmax]; FR_EINVAL otherwise). */
+int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double* host_u);
+/* Connectivity tables, host arrays of M*2*dim entries. */
+int fr_get_conn(fr_mesh* m, int32_t* host_nbr, int8_t* host_ftype, int8_t* host_slot, int64_t cap);
+/* Replaces the state with the closed-form vortex at time t on the current tree and sets time. */
+int fr_set_exact(fr_mesh* m, double t);
+int fr_set_time(fr_mesh* m, double t);
+int fr_get_info(fr_mesh* m, fr_info* out);
+const char* fr_last_error(const fr_mesh* m);
+
+/* Measurement.  With profiling on, every interface and element kernel launched by fr_step,
+   fr_run and fr_rhs is bracketed by CUDA events on the mesh's stream; fr_profile_read
+   synchronises, sums the event intervals and returns them with the work those launches did.
+   fr_profile_enable(m, 1) (re)starts the counters, fr_profile_enable(m, 0) stops recording. */
+typedef struct {
+  int64_t stage_launches, face_launches;
+  double stage_ms, face_ms;   /* summed device time of those launches                     */
+  int64_t stage_points;       /* solution points processed by the element kernel launches  */
+  int64_t face_points;        /* face (mortar) points processed by the interface launches  */
+  int64_t kernel_launches;    /* every kernel this library launched since enable           */
+} fr_profile;
+int fr_profile_enable(fr_mesh* m, int on);
+int fr_profile_read(fr_mesh* m, fr_profile* out);
+/* Process-wide number of kernels this library has launched (all meshes and primitives). */
+int64_t fr_kernel_launches(void);
+
+/* ---------------------------------------------------------------------------------------------
+ * Tree primitives on caller-owned DEVICE arrays, stream-ordered on `stream`.  Scratch memory is
+ * allocated with cudaMallocAsync on the stream and released before return.  Counts that size an
+ * output are returned through host pointers (the call synchronises the stream for them).
+ * ------------------------------------------------------------------------------------------- */
+
+/* Algorithm 1 (Sec. 2.2): boxes int32[n][4] -> keys uint64[n]. */
+int fr_morton_encode(int dim, int Dmax, int64_t n, const int32_t* d_boxes, uint64_t* d_keys,
+                     void* stream);
+/* Ascending LSD radix sort of keys in place over the dim*Dmax+m_b significant bits. */
+int fr_keys_sort(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream);
+/* Sort, then linearise (Sec. 3.1): drop duplicates and octants that have a descendant in the set.
+   d_out may alias nothing; *n_out receives the count (FR_EOVERFLOW if > cap). */
+int fr_keys_linearise(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,
+                      int64_t cap, int64_t* n_out, void* stream);
+/* 2:1 balance (Sec. 3.2, strong/vertex balance, periodic) of a complete sorted linear tree: the
+   coarsest balanced refinement.  Depth passes from Dmax down to 2. */
+int fr_tree_balance(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,
+                    int64_t cap, int64_t* n_out, void* stream);
+/* Adaptation procedure (Sec. 4.1) with flags int8[n], then 2:1 balance down to depth Dbase+2. */
+int fr_tree_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys, const int8_t* d_flags,
+                  int64_t n, uint64_t* d_out, int64_t cap, int64_t* n_out, void* stream);
+/* Old->new mapping (Sec. 4.2): src int32[n_new], tag int8[n_new] (0 copy, 1 refined from the old
+   leaf src, 2 fused from the 2^dim old leaves starting at src). */
+int fr_tree_map(int dim, int Dmax, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
+                int64_t n_new, int32_t* d_src, int8_t* d_tag, void* stream);
+/* Face connectivity (Sec. 3.3) of a complete sorted 2:1-balanced tree: nbr/ftype/slot [n][2dim]. */
+int fr_tree_conn(int dim, int Dmax, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+                 int8_t* d_ftype, int8_t* d_slot, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,847 @@
+// fr_api.cu -- the C ABI of include/fr.h: mesh object, time stepping, adaptation orchestration
+// (flags -> edit -> 2:1 balance -> mapping -> transfer -> connectivity), face lists, host I/O and
+// the device-array tree primitives.
+#include <cmath>
+#include <cstring>
+
+#include "fr_internal.cuh"
+#include "fr_solver.cuh"
+
+using namespace frg;
+
+struct fr_mesh {
+  Err err;
+  fr_config cfg{};
+  std::vector<double> vort;
+  int dim = 2, p = 1, n = 2, N = 4, Nf = 2, nv = 4, nfc = 4, EU = 16, EF = 32;
+  KG g{};
+  DevOps ops{};
+  DevProblem prob{};
+  cudaStream_t stream = nullptr;
+  fr_allocator user{};
+  bool has_user = false;
+  Alloc A;
+  double t = 0.0, dt = 0.0;
+  int64_t step = 0, M = 0;
+  Buf<uint64_t> keys;
+  Buf<double> u, w, trace, fcomm;
+  Buf<int32_t> nbr, conf, hang, contrib;
+  Buf<int8_t> ftype, slot, flags;
+  int64_t n_conf = 0, n_hang = 0;
+  Buf<double> norm_part, norm_out;
+  Buf<unsigned long long> dmax;
+  // measurement: event pairs around interface (kind 0) and element (kind 1) launches
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+    int64_t points;
+  };
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<Rec> recs;
+  int64_t launches0 = 0;
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+};
+
+namespace {
+
+constexpr int TB = 256;
+inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); }
+
+// faces per element: conforming faces owned by their minus side (checked on the plus face of
+// each element), coarse sides of hanging faces
+template <int DIM>
+__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int32_t* __restrict__ cc,
+                             int32_t* __restrict__ ch) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  int a = 0, b = 0;
+#pragma unroll
+  for (int f = 0; f < 2 * DIM; ++f) {
+    int8_t t = ftype[e * 2 * DIM + f];
+    a += (f & 1) && t == 0;
+    b += t == 2;
+  }
+  cc[e] = a;
+  ch[e] = b;
+}
+
+template <int DIM>
+__global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
+                             int64_t M, const int64_t* __restrict__ oc, const int64_t* __restrict__ oh,
+                             int32_t* __restrict__ conf, int32_t* __restrict__ hang,
+                             int32_t* __restrict__ hcon) {
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  int64_t a = oc[e], b = oh[e];
+#pragma unroll
+  for (int f = 0; f < 2 * DIM; ++f) {
+    int8_t t = ftype[e * 2 * DIM + f];
+    if ((f & 1) && t == 0) conf[a++] = int32_t((e << 2) | (f >> 1));
+    if (t == 2) {
+      hang[b] = int32_t((e << 3) | f);
+      for (int s = 0; s < 4; ++s) hcon[b * 4 + s] = contrib[(e * 2 * DIM + f) * 4 + s];
+      ++b;
+    }
+  }
+}
+
+int check_cfg(const fr_config* c, Err* err) {
+  if (!c) return set_error(err, FR_EINVAL, "null config");
+  if (c->dim != 2 && c->dim != 3) return set_error(err, FR_EINVAL, "dim must be 2 or 3");
+  if (c->p < 1 || c->p > 4) return set_error(err, FR_EINVAL, "p must be in 1..4");
+  if (c->Dmax < 1 || c->Dmax > 30) return set_error(err, FR_EINVAL, "Dmax out of range");
+  if (c->dim * c->Dmax + depth_bits(c->Dmax) > 63)
+    return set_error(err, FR_EINVAL, "dim*Dmax + depth bits exceeds 63");
+  if (c->dim == 3 && c->Dmax > 19) return set_error(err, FR_EINVAL, "Dmax > 19 in 3D");
+  if (c->Dbase < 1 || c->Dbase > c->Dmax) return set_error(err, FR_EINVAL, "Dbase out of range");
+  if (int64_t(1) << (c->dim * c->Dbase) > (int64_t(1) << 30))
+    return set_error(err, FR_EINVAL, "base level too large");
+  if (!(c->L > 0) || !(c->gamma > 1.0) || !(c->rho_inf > 0) || !(c->p_inf > 0))
+    return set_error(err, FR_EINVAL, "L, gamma, rho_inf, p_inf must be positive (gamma > 1)");
+  if (c->nvort < 0 || c->nvort > 16 || (c->nvort > 0 && !c->vort))
+    return set_error(err, FR_EINVAL, "nvort must be in 0..16 with a vortex array");
+  if (c->indicator < 0 || c->indicator > 2) return set_error(err, FR_EINVAL, "bad indicator");
+  if (c->precision != 0) return set_error(err, FR_EINVAL, "only precision 0 (FP64) is implemented");
+  if (!(c->dt > 0) && !(c->cfl > 0)) return set_error(err, FR_EINVAL, "need dt > 0 or cfl > 0");
+  return 0;
+}
+
+int rebuild_conn(fr_mesh* m) {
+  Err* err = &m->err;
+  cudaStream_t s = m->stream;
+  int64_t M = m->M, S = M * m->nfc;
+  FR_TRY(m->nbr.ensure(m->A, S));
+  FR_TRY(m->ftype.ensure(m->A, S));
+  FR_TRY(m->slot.ensure(m->A, S));
+  FR_TRY(m->contrib.ensure(m->A, S * 4));
+  Scratch Sc(&m->A);
+  int32_t* bad = Sc.get<int32_t>(1);
+  int32_t* cc = Sc.get<int32_t>(M);
+  int32_t* ch = Sc.get<int32_t>(M);
+  int64_t* oc = Sc.get<int64_t>(M);
+  int64_t* oh = Sc.get<int64_t>(M);
+  int64_t* tot = Sc.get<int64_t>(2);
+  if (!bad || !cc || !ch || !oc || !oh || !tot) return set_error(err, FR_ENOMEM, "conn scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  FR_CUDA(err, cudaMemsetAsync(m->contrib.p, 0xff, size_t(S) * 16, s));
+  FR_TRY(tree_conn(m->dim, m->g, m->keys.p, M, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
+  if (m->dim == 2)
+    k_face_count<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cc, ch);
+  else
+    k_face_count<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cc, ch);
+  FR_LAUNCH_CHECK(err);
+  FR_TRY(scan_counts(cc, oc, M, tot, Sc, s, err));
+  FR_TRY(scan_counts(ch, oh, M, tot + 1, Sc, s, err));
+  int64_t h[2];
+  int32_t hb = 0;
+  FR_CUDA(err, cudaMemcpyAsync(h, tot, 16, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  if (hb) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
+  m->n_conf = h[0];
+  m->n_hang = h[1];
+  FR_TRY(m->conf.ensure(m->A, m->n_conf));
+  FR_TRY(m->hang.ensure(m->A, m->n_hang));
+  Buf<int32_t> hcon;
+  FR_TRY(hcon.ensure(m->A, m->n_hang * 4));
+  if (m->dim == 2)
+    k_face_write<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, oc, oh, m->conf.p, m->hang.p, hcon.p);
+  else
+    k_face_write<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, oc, oh, m->conf.p, m->hang.p, hcon.p);
+  FR_LAUNCH_CHECK(err);
+  // keep the per-hanging-face contributor table in `contrib` (per element-face table is not
+  // needed after the lists are built)
+  Buf<int32_t> old = m->contrib;
+  m->contrib = hcon;
+  old.release(m->A);
+  return 0;
+}
+
+int ensure_state(fr_mesh* m, int64_t M) {
+  FR_TRY(m->u.ensure(m->A, size_t(M) * m->EU));
+  FR_TRY(m->w.ensure(m->A, size_t(M) * m->EU));
+  FR_TRY(m->trace.ensure(m->A, size_t(M) * m->EF));
+  FR_TRY(m->fcomm.ensure(m->A, size_t(M) * m->EF));
+  FR_TRY(m->flags.ensure(m->A, size_t(M)));
+  return 0;
+}
+
+int refresh_traces(fr_mesh* m) {
+  return launch_traces(m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err);
+}
+
+FaceArgs face_args(fr_mesh* m) {
+  FaceArgs A{};
+  A.trace = m->trace.p;
+  A.fcomm = m->fcomm.p;
+  A.nbr = m->nbr.p;
+  A.conf = m->conf.p;
+  A.hang = m->hang.p;
+  A.contrib = m->contrib.p;
+  A.n_conf = m->n_conf;
+  A.n_hang = m->n_hang;
+  A.gamma = m->cfg.gamma;
+  return A;
+}
+
+int stage(fr_mesh* m, const double* us, const double* un, double* out, double a, double b, double c,
+          bool traces) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  if (m->prof) {
+    e0 = m->next_event();
+    e1 = m->next_event();
+    e2 = m->next_event();
+    cudaEventRecord(e0, m->stream);
+  }
+  FR_TRY(launch_faces(m->dim, m->p, face_args(m), m->ops, m->stream, &m->err));
+  if (m->prof) {
+    cudaEventRecord(e1, m->stream);
+    int64_t nsub = int64_t(1) << (m->dim - 1);
+    m->recs.push_back({0, e0, e1, (m->n_conf + m->n_hang * nsub) * m->Nf});
+  }
+  StageArgs S{};
+  S.keys = m->keys.p;
+  S.us = us;
+  S.un = un;
+  S.fcomm = m->fcomm.p;
+  S.out = out;
+  S.trace_out = traces ? m->trace.p : nullptr;
+  S.M = m->M;
+  S.g = m->g;
+  S.L = m->cfg.L;
+  S.gamma = m->cfg.gamma;
+  S.a = a;
+  S.b = b;
+  S.c = c;
+  FR_TRY(launch_stage(m->dim, m->p, S, m->ops, m->stream, &m->err));
+  if (m->prof) {
+    cudaEventRecord(e2, m->stream);
+    m->recs.push_back({1, e1, e2, m->M * m->N});
+  }
+  return 0;
+}
+
+// one SSP-RK3 step (Eq. rk3): u1 = u + dt R(u); u2 = 3/4 u + 1/4 u1 + 1/4 dt R(u1);
+// u^{n+1} = 1/3 u + 2/3 u2 + 2/3 dt R(u2).  Buffers: u holds u^n, w holds u1 then u2.
+int rk3_step(fr_mesh* m) {
+  double dt = m->dt;
+  FR_TRY(stage(m, m->u.p, nullptr, m->w.p, 0.0, 1.0, dt, true));
+  FR_TRY(stage(m, m->w.p, m->u.p, m->w.p, 0.75, 0.25, 0.25 * dt, true));
+  FR_TRY(stage(m, m->w.p, m->u.p, m->u.p, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true));
+  m->t += dt;
+  m->step += 1;
+  return 0;
+}
+
+int compute_flags(fr_mesh* m, double* eta) {
+  if (m->cfg.indicator == 2) {
+    FR_CUDA(&m->err, cudaMemsetAsync(m->flags.p, 0, size_t(m->M), m->stream));
+    return 0;
+  }
+  return launch_indicator(m->dim, m->p, m->cfg.indicator, m->cfg.th_refine, m->cfg.th_coarsen,
+                          m->t, m->keys.p, m->M, m->g, m->prob, m->ops, m->u.p, m->flags.p, eta,
+                          m->stream, &m->err);
+}
+
+struct Timer {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool on;
+  cudaStream_t s;
+  Timer(bool enable, cudaStream_t st) : on(enable), s(st) {
+    if (on)
+      for (auto& x : e) cudaEventCreate(&x);
+  }
+  ~Timer() {
+    if (on)
+      for (auto& x : e) cudaEventDestroy(x);
+  }
+  void mark(int k) {
+    if (on) cudaEventRecord(e[k], s);
+  }
+  double ms(int a, int b) {
+    if (!on) return 0.0;
+    float v = 0.f;
+    cudaEventSynchronize(e[b]);
+    cudaEventElapsedTime(&v, e[a], e[b]);
+    return double(v);
+  }
+};
+
+// Adaptation: edit the tree with the flags, balance, and (if `transfer`) carry the state over.
+int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool transfer) {
+  Err* err = &m->err;
+  cudaStream_t s = m->stream;
+  Timer T(st != nullptr, s);
+  T.mark(0);
+  const int8_t* fl = d_flags;
+  if (!fl) {
+    FR_TRY(compute_flags(m, nullptr));
+    fl = m->flags.p;
+  }
+  Buf<uint64_t> nk;
+  int64_t M1 = 0, nref = 0, ncoarse = 0;
+  int passes = 0;
+  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, m->M, nk, &M1, &nref, &ncoarse, m->A, s, err);
+  if (!rc) rc = tree_balance(m->dim, m->g, m->cfg.Dbase + 2, nk, &M1, &passes, m->A, s, err);
+  if (rc) {
+    nk.release(m->A);
+    return rc;
+  }
+  Buf<double> nu;
+  Buf<int32_t> src;
+  Buf<int8_t> tag;
+  Scratch Sc(&m->A);
+  if (transfer) {
+    int32_t* bad = Sc.get<int32_t>(1);
+    if (!bad) rc = set_error(err, FR_ENOMEM, "adapt scratch");
+    if (!rc) rc = src.ensure(m->A, M1);
+    if (!rc) rc = tag.ensure(m->A, M1);
+    if (!rc) rc = cudaMemsetAsync(bad, 0, 4, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "memset");
+    if (!rc) rc = tree_map(m->dim, m->g, m->keys.p, m->M, nk.p, M1, src.p, tag.p, bad, s, err);
+    T.mark(1);
+    if (!rc) rc = nu.ensure(m->A, size_t(M1) * m->EU);
+    if (!rc) rc = launch_transfer(m->dim, m->p, m->g, m->keys.p, nk.p, src.p, tag.p, M1, m->ops, m->u.p, nu.p, s, err);
+    int32_t hb = 0;
+    if (!rc && cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess && hb)
+      rc = set_error(err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
+  } else {
+    T.mark(1);
+  }
+  T.mark(2);
+  src.release(m->A);
+  tag.release(m->A);
+  if (rc) {
+    nk.release(m->A);
+    nu.release(m->A);
+    return rc;
+  }
+  int64_t M0 = m->M;
+  Buf<uint64_t> ok = m->keys;
+  m->keys = nk;
+  ok.release(m->A);
+  m->M = M1;
+  if (transfer) {
+    Buf<double> ou = m->u;
+    m->u = nu;
+    ou.release(m->A);
+  }
+  FR_TRY(m->w.ensure(m->A, size_t(M1) * m->EU));
+  FR_TRY(m->trace.ensure(m->A, size_t(M1) * m->EF));
+  FR_TRY(m->fcomm.ensure(m->A, size_t(M1) * m->EF));
+  FR_TRY(m->flags.ensure(m->A, size_t(M1)));
+  if (!transfer) FR_TRY(m->u.ensure(m->A, size_t(M1) * m->EU));
+  FR_TRY(rebuild_conn(m));
+  if (transfer) FR_TRY(refresh_traces(m));
+  T.mark(3);
+  if (st) {
+    st->M_old = M0;
+    st->M_new = M1;
+    st->n_refined = nref;
+    st->n_coarsened = ncoarse;
+    st->balance_passes = passes;
+    st->ms_tree = T.ms(0, 1);
+    st->ms_transfer = T.ms(1, 2);
+    st->ms_conn = T.ms(2, 3);
+  }
+  return 0;
+}
+
+int set_exact(fr_mesh* m, double t) {
+  FR_TRY(launch_exact(m->dim, m->p, m->keys.p, m->M, m->g, t, m->prob, m->ops, m->u.p, m->stream, &m->err));
+  m->t = t;
+  return 0;
+}
+
+int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void* stream) {
+  Err* err = &m->err;
+  FR_TRY(check_cfg(cfg, err));
+  m->cfg = *cfg;
+  m->vort.assign(cfg->vort, cfg->vort + 4 * cfg->nvort);
+  m->cfg.vort = m->vort.data();
+  m->dim = cfg->dim;
+  m->p = cfg->p;
+  m->n = cfg->p + 1;
+  m->N = m->dim == 2 ? m->n * m->n : m->n * m->n * m->n;
+  m->Nf = m->dim == 2 ? m->n : m->n * m->n;
+  m->nv = m->dim + 2;
+  m->nfc = 2 * m->dim;
+  m->EU = m->nv * m->N;
+  m->EF = m->nfc * m->nv * m->Nf;
+  m->g = KG{cfg->Dmax, depth_bits(cfg->Dmax)};
+  if (build_ops(m->p, &m->ops)) return set_error(err, FR_EINVAL, "operators");
+  m->prob = DevProblem{};
+  m->prob.L = cfg->L;
+  m->prob.gamma = cfg->gamma;
+  m->prob.rho_inf = cfg->rho_inf;
+  m->prob.p_inf = cfg->p_inf;
+  for (int a = 0; a < 3; ++a) m->prob.uinf[a] = cfg->uinf[a];
+  m->prob.nvort = cfg->nvort;
+  for (int k = 0; k < cfg->nvort; ++k)
+    for (int j = 0; j < 4; ++j) m->prob.vort[k][j] = cfg->vort[4 * k + j];
+  m->stream = static_cast<cudaStream_t>(stream);
+  if (alloc) {
+    m->user = *alloc;
+    m->has_user = true;
+  }
+  m->A = Alloc{m->has_user ? &m->user : nullptr, m->stream, err};
+  int devcount = 0;
+  if (cudaGetDeviceCount(&devcount) != cudaSuccess || devcount == 0) {
+    cudaGetLastError();
+    return set_error(err, FR_ECUDA, "no CUDA device");
+  }
+  // uniform tree at Dbase, then passes of {closed form, flags, adapt}
+  m->M = int64_t(1) << (m->dim * cfg->Dbase);
+  FR_TRY(m->keys.ensure(m->A, m->M));
+  FR_TRY(tree_uniform(m->dim, m->g, cfg->Dbase, m->keys.p, m->stream, err));
+  FR_TRY(ensure_state(m, m->M));
+  int passes = cfg->init_passes < 0 ? cfg->Dmax - cfg->Dbase : cfg->init_passes;
+  for (int ps = 0; ps < passes; ++ps) {
+    FR_TRY(set_exact(m, 0.0));
+    if (cfg->indicator == 2) break;
+    FR_TRY(compute_flags(m, nullptr));
+    FR_TRY(adapt_impl(m, m->flags.p, nullptr, false));
+  }
+  FR_TRY(set_exact(m, 0.0));
+  if (passes == 0 || cfg->indicator == 2) FR_TRY(rebuild_conn(m));
+  FR_TRY(refresh_traces(m));
+  if (cfg->dt > 0) {
+    m->dt = cfg->dt;
+  } else {
+    FR_TRY(m->dmax.ensure(m->A, 1));
+    FR_TRY(launch_maxspeed(m->dim, m->p, m->u.p, m->M, cfg->gamma, m->dmax.p, m->stream, err));
+    unsigned long long bits = 0;
+    FR_CUDA(err, cudaMemcpyAsync(&bits, m->dmax.p, 8, cudaMemcpyDeviceToHost, m->stream));
+    FR_CUDA(err, cudaStreamSynchronize(m->stream));
+    double smax;
+    std::memcpy(&smax, &bits, 8);
+    double hmin = cfg->L / double(int64_t(1) << cfg->Dmax);
+    m->dt = cfg->cfl * hmin / ((2.0 * cfg->p + 1.0) * smax);
+  }
+  m->t = 0.0;
+  m->step = 0;
+  FR_CUDA(err, cudaStreamSynchronize(m->stream));
+  return 0;
+}
+
+void free_all(fr_mesh* m) {
+  m->keys.release(m->A);
+  m->u.release(m->A);
+  m->w.release(m->A);
+  m->trace.release(m->A);
+  m->fcomm.release(m->A);
+  m->nbr.release(m->A);
+  m->conf.release(m->A);
+  m->hang.release(m->A);
+  m->contrib.release(m->A);
+  m->ftype.release(m->A);
+  m->slot.release(m->A);
+  m->flags.release(m->A);
+  m->norm_part.release(m->A);
+  m->norm_out.release(m->A);
+  m->dmax.release(m->A);
+}
+
+int host_copy(Err* err, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {
+  if (bytes == 0) return 0;
+  FR_CUDA(err, cudaMemcpyAsync(dst, src, bytes, kind, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  return 0;
+}
+
+KG geo_or_err(int dim, int Dmax, int* rc) {
+  *rc = 0;
+  if ((dim != 2 && dim != 3) || Dmax < 1 || Dmax > 30 || dim * Dmax + depth_bits(Dmax) > 63 ||
+      (dim == 3 && Dmax > 19))
+    *rc = set_error(global_err(), FR_EINVAL, "dim/Dmax out of range");
+  return KG{Dmax, depth_bits(Dmax)};
+}
+
+}  // namespace
+
+// =============================================================================================
+extern "C" {
+
+const char* fr_last_error(const fr_mesh* m) {
+  return m ? m->err.msg.c_str() : global_err()->msg.c_str();
+}
+
+int fr_mesh_init(const fr_config* cfg, const fr_allocator* alloc, void* stream, fr_mesh** out) {
+  if (!out) return set_error(global_err(), FR_EINVAL, "null output handle");
+  *out = nullptr;
+  fr_mesh* m = new fr_mesh();
+  int rc = init_impl(m, cfg, alloc, stream);
+  if (rc) {
+    *global_err() = m->err;
+    free_all(m);
+    delete m;
+    return rc;
+  }
+  *out = m;
+  return 0;
+}
+
+void fr_mesh_free(fr_mesh* m) {
+  if (!m) return;
+  free_all(m);
+  cudaStreamSynchronize(m->stream);
+  for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
+  delete m;
+}
+
+int fr_step(fr_mesh* m, int nsteps, fr_step_stats* st) {
+  if (!m || nsteps < 0) return set_error(m ? &m->err : global_err(), FR_EINVAL, "bad arguments");
+  Timer T(st != nullptr, m->stream);
+  T.mark(0);
+  for (int k = 0; k < nsteps; ++k) FR_TRY(rk3_step(m));
+  T.mark(1);
+  if (st) {
+    st->steps = nsteps;
+    st->dof_updates = int64_t(nsteps) * m->M * m->N * m->nv;
+    st->ms = T.ms(0, 1);
+  }
+  return 0;
+}
+
+int fr_run(fr_mesh* m, int nsteps, fr_step_stats* sst, fr_adapt_stats* ast) {
+  if (!m || nsteps < 0) return set_error(m ? &m->err : global_err(), FR_EINVAL, "bad arguments");
+  fr_step_stats acc{};
+  fr_adapt_stats aacc{};
+  for (int k = 0; k < nsteps; ++k) {
+    fr_step_stats one{};
+    FR_TRY(fr_step(m, 1, sst ? &one : nullptr));
+    acc.steps += one.steps;
+    acc.dof_updates += one.dof_updates;
+    acc.ms += one.ms;
+    if (m->cfg.adapt_every > 0 && m->step % m->cfg.adapt_every == 0) {
+      fr_adapt_stats a{};
+      FR_TRY(adapt_impl(m, nullptr, ast ? &a : nullptr, true));
+      aacc.M_old = a.M_old;
+      aacc.M_new = a.M_new;
+      aacc.n_refined += a.n_refined;
+      aacc.n_coarsened += a.n_coarsened;
+      aacc.balance_passes += a.balance_passes;
+      aacc.ms_tree += a.ms_tree;
+      aacc.ms_transfer += a.ms_transfer;
+      aacc.ms_conn += a.ms_conn;
+    }
+  }
+  if (sst) *sst = acc;
+  if (ast) *ast = aacc;
+  return 0;
+}
+
+int fr_adapt(fr_mesh* m, const int8_t* dev_flags, fr_adapt_stats* st) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  return adapt_impl(m, dev_flags, st, true);
+}
+
+int fr_flags(fr_mesh* m, int8_t* host_flags, double* host_eta, int64_t cap) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  if (cap < m->M) return set_error(&m->err, FR_EOVERFLOW, "capacity below M");
+  Buf<double> eta;
+  if (host_eta) FR_TRY(eta.ensure(m->A, m->M));
+  if (m->cfg.indicator == 2) {
+    FR_CUDA(&m->err, cudaMemsetAsync(m->flags.p, 0, size_t(m->M), m->stream));
+    if (host_eta) FR_CUDA(&m->err, cudaMemsetAsync(eta.p, 0, size_t(m->M) * 8, m->stream));
+  } else {
+    FR_TRY(compute_flags(m, host_eta ? eta.p : nullptr));
+  }
+  int rc = host_copy(&m->err, host_flags, m->flags.p, size_t(m->M), cudaMemcpyDeviceToHost, m->stream);
+  if (!rc && host_eta)
+    rc = host_copy(&m->err, host_eta, eta.p, size_t(m->M) * 8, cudaMemcpyDeviceToHost, m->stream);
+  eta.release(m->A);
+  return rc;
+}
+
+int fr_rhs(fr_mesh* m, double* host_R, int64_t cap) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  int64_t S = m->M * m->EU;
+  if (cap < S) return set_error(&m->err, FR_EOVERFLOW, "capacity below M*nv*N");
+  FR_TRY(stage(m, m->u.p, nullptr, m->w.p, 0.0, 0.0, 1.0, false));
+  return host_copy(&m->err, host_R, m->w.p, size_t(S) * 8, cudaMemcpyDeviceToHost, m->stream);
+}
+
+int fr_norms(fr_mesh* m, fr_norms_out* out) {
+  if (!m || !out) return set_error(m ? &m->err : global_err(), FR_EINVAL, "null argument");
+  int64_t nb = norms_blocks(m->dim, m->p, m->M);
+  FR_TRY(m->norm_part.ensure(m->A, size_t(nb + 1) * 8));
+  FR_TRY(m->norm_out.ensure(m->A, 8));
+  FR_TRY(launch_norms(m->dim, m->p, m->keys.p, m->M, m->g, m->t, m->prob, m->ops, m->u.p,
+                      m->norm_part.p, nb + 1, m->norm_out.p, m->stream, &m->err));
+  double h[8];
+  FR_TRY(host_copy(&m->err, h, m->norm_out.p, 64, cudaMemcpyDeviceToHost, m->stream));
+  out->t = m->t;
+  out->l2_rho = std::sqrt(h[0]);
+  for (int v = 0; v < 5; ++v) out->integral[v] = v < m->nv ? h[1 + v] : 0.0;
+  out->min_rho = h[m->nv + 1];
+  out->min_p = h[m->nv + 2];
+  out->M = m->M;
+  return 0;
+}
+
+int fr_get_leaves(fr_mesh* m, uint64_t* host_keys, int64_t cap, int64_t* M) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  if (M) *M = m->M;
+  if (!host_keys) return 0;
+  if (cap < m->M) return set_error(&m->err, FR_EOVERFLOW, "capacity below M");
+  return host_copy(&m->err, host_keys, m->keys.p, size_t(m->M) * 8, cudaMemcpyDeviceToHost, m->stream);
+}
+
+int fr_get_state(fr_mesh* m, double* host_u, int64_t cap) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  int64_t S = m->M * m->EU;
+  if (cap < S) return set_error(&m->err, FR_EOVERFLOW, "capacity below M*nv*N");
+  return host_copy(&m->err, host_u, m->u.p, size_t(S) * 8, cudaMemcpyDeviceToHost, m->stream);
+}
+
+int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double* host_u) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  if (M <= 0 || !host_keys || !host_u) return set_error(&m->err, FR_EINVAL, "bad arguments");
+  Buf<uint64_t> nk;
+  FR_TRY(nk.ensure(m->A, M));
+  FR_TRY(host_copy(&m->err, nk.p, host_keys, size_t(M) * 8, cudaMemcpyHostToDevice, m->stream));
+  bool ok = false;
+  int rc = tree_validate(m->dim, m->g, nk.p, M, m->cfg.Dbase, m->cfg.Dmax, &ok, m->A, m->stream, &m->err);
+  if (!rc && !ok) rc = set_error(&m->err, FR_EINVAL, "keys are not a complete sorted linear tree in [Dbase, Dmax]");
+  if (rc) {
+    nk.release(m->A);
+    return rc;
+  }
+  Buf<uint64_t> old = m->keys;
+  int64_t oldM = m->M;
+  m->keys = nk;
+  m->M = M;
+  rc = ensure_state(m, M);
+  if (!rc) rc = rebuild_conn(m);
+  if (rc) {
+    // restore the previous tree
+    m->keys = old;
+    m->M = oldM;
+    nk.release(m->A);
+    int rc2 = rebuild_conn(m);
+    (void)rc2;
+    return rc;
+  }
+  old.release(m->A);
+  FR_TRY(host_copy(&m->err, m->u.p, host_u, size_t(M) * m->EU * 8, cudaMemcpyHostToDevice, m->stream));
+  return refresh_traces(m);
+}
+
+int fr_get_conn(fr_mesh* m, int32_t* nbr, int8_t* ftype, int8_t* slot, int64_t cap) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  int64_t S = m->M * m->nfc;
+  if (cap < S) return set_error(&m->err, FR_EOVERFLOW, "capacity below M*2*dim");
+  FR_TRY(host_copy(&m->err, nbr, m->nbr.p, size_t(S) * 4, cudaMemcpyDeviceToHost, m->stream));
+  FR_TRY(host_copy(&m->err, ftype, m->ftype.p, size_t(S), cudaMemcpyDeviceToHost, m->stream));
+  return host_copy(&m->err, slot, m->slot.p, size_t(S), cudaMemcpyDeviceToHost, m->stream);
+}
+
+int fr_set_exact(fr_mesh* m, double t) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  FR_TRY(set_exact(m, t));
+  return refresh_traces(m);
+}
+
+int fr_set_time(fr_mesh* m, double t) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  m->t = t;
+  return 0;
+}
+
+int fr_get_info(fr_mesh* m, fr_info* out) {
+  if (!m || !out) return set_error(m ? &m->err : global_err(), FR_EINVAL, "null argument");
+  out->t = m->t;
+  out->dt = m->dt;
+  out->M = m->M;
+  out->step = m->step;
+  out->dim = m->dim;
+  out->p = m->p;
+  out->nv = m->nv;
+  out->N = m->N;
+  out->n_conforming = m->n_conf;
+  out->n_hanging = m->n_hang;
+  return 0;
+}
+
+int fr_profile_enable(fr_mesh* m, int on) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  FR_CUDA(&m->err, cudaStreamSynchronize(m->stream));
+  m->prof = on != 0;
+  m->recs.clear();
+  m->ev_used = 0;
+  m->launches0 = launch_counter();
+  return 0;
+}
+
+int fr_profile_read(fr_mesh* m, fr_profile* out) {
+  if (!m || !out) return set_error(m ? &m->err : global_err(), FR_EINVAL, "null argument");
+  FR_CUDA(&m->err, cudaStreamSynchronize(m->stream));
+  *out = fr_profile{};
+  for (const auto& r : m->recs) {
+    float ms = 0.f;
+    FR_CUDA(&m->err, cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.kind == 0) {
+      out->face_launches += 1;
+      out->face_ms += ms;
+      out->face_points += r.points;
+    } else {
+      out->stage_launches += 1;
+      out->stage_ms += ms;
+      out->stage_points += r.points;
+    }
+  }
+  out->kernel_launches = launch_counter() - m->launches0;
+  return 0;
+}
+
+int64_t fr_kernel_launches(void) { return launch_counter(); }
+
+// ---- tree primitives on caller-owned device arrays ----
+
+int fr_morton_encode(int dim, int Dmax, int64_t n, const int32_t* d_boxes, uint64_t* d_keys,
+                     void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n < 0) return set_error(global_err(), FR_EINVAL, "n < 0");
+  return tree_encode(dim, g, d_boxes, n, d_keys, static_cast<cudaStream_t>(stream), global_err());
+}
+
+int fr_keys_sort(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n < 0) return set_error(global_err(), FR_EINVAL, "n < 0");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Alloc A{nullptr, s, global_err()};
+  Scratch S(&A);
+  uint64_t* tmp = S.get<uint64_t>(n);
+  if (!tmp) return set_error(global_err(), FR_ENOMEM, "sort scratch");
+  FR_TRY(radix_sort_keys(d_keys, tmp, n, dim * Dmax + g.mb, S, s, global_err()));
+  FR_CUDA(global_err(), cudaStreamSynchronize(s));
+  return 0;
+}
+
+int fr_keys_linearise(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,
+                      int64_t cap, int64_t* n_out, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n < 0 || !n_out) return set_error(global_err(), FR_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Err* err = global_err();
+  Alloc A{nullptr, s, err};
+  Scratch S(&A);
+  uint64_t* a = S.get<uint64_t>(n);
+  uint64_t* tmp = S.get<uint64_t>(n);
+  if (!a || !tmp) return set_error(err, FR_ENOMEM, "linearise scratch");
+  if (n) FR_CUDA(err, cudaMemcpyAsync(a, d_keys, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+  FR_TRY(radix_sort_keys(a, tmp, n, dim * Dmax + g.mb, S, s, err));
+  Buf<uint64_t> out;
+  int64_t m = 0;
+  rc = tree_linearise(dim, g, a, n, out, &m, A, s, err);
+  *n_out = m;
+  if (!rc && m > cap) rc = set_error(err, FR_EOVERFLOW, "output capacity too small");
+  if (!rc && m) rc = cudaMemcpyAsync(d_out, out.p, size_t(m) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
+  out.release(A);
+  if (!rc) FR_CUDA(err, cudaStreamSynchronize(s));
+  return rc;
+}
+
+static int balance_or_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys, const int8_t* d_flags,
+                            int64_t n, uint64_t* d_out, int64_t cap, int64_t* n_out, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n <= 0 || !n_out) return set_error(global_err(), FR_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Err* err = global_err();
+  Alloc A{nullptr, s, err};
+  bool ok = false;
+  FR_TRY(tree_validate(dim, g, d_keys, n, 0, Dmax, &ok, A, s, err));
+  if (!ok) return set_error(err, FR_EINVAL, "input is not a complete sorted linear tree");
+  Buf<uint64_t> k;
+  int64_t m = n;
+  if (d_flags) {
+    rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, &m, nullptr, nullptr, A, s, err);
+  } else {
+    rc = k.ensure(A, n);
+    if (!rc) rc = cudaMemcpyAsync(k.p, d_keys, size_t(n) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
+  }
+  if (!rc) rc = tree_balance(dim, g, d_flags ? Dbase + 2 : 2, k, &m, nullptr, A, s, err);
+  *n_out = m;
+  if (!rc && m > cap) rc = set_error(err, FR_EOVERFLOW, "output capacity too small");
+  if (!rc) rc = cudaMemcpyAsync(d_out, k.p, size_t(m) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
+  k.release(A);
+  if (!rc) FR_CUDA(err, cudaStreamSynchronize(s));
+  return rc;
+}
+
+int fr_tree_balance(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,
+                    int64_t cap, int64_t* n_out, void* stream) {
+  return balance_or_adapt(dim, 0, Dmax, d_keys, nullptr, n, d_out, cap, n_out, stream);
+}
+
+int fr_tree_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys, const int8_t* d_flags,
+                  int64_t n, uint64_t* d_out, int64_t cap, int64_t* n_out, void* stream) {
+  if (!d_flags) return set_error(global_err(), FR_EINVAL, "null flags");
+  if (Dbase < 0 || Dbase > Dmax) return set_error(global_err(), FR_EINVAL, "Dbase out of range");
+  return balance_or_adapt(dim, Dbase, Dmax, d_keys, d_flags, n, d_out, cap, n_out, stream);
+}
+
+int fr_tree_map(int dim, int Dmax, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
+                int64_t n_new, int32_t* d_src, int8_t* d_tag, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n_old <= 0 || n_new < 0) return set_error(global_err(), FR_EINVAL, "bad sizes");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Err* err = global_err();
+  Alloc A{nullptr, s, err};
+  Scratch S(&A);
+  int32_t* bad = S.get<int32_t>(1);
+  if (!bad) return set_error(err, FR_ENOMEM, "map scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  FR_TRY(tree_map(dim, g, d_old, n_old, d_new, n_new, d_src, d_tag, bad, s, err));
+  int32_t hb = 0;
+  FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  if (hb) return set_error(err, FR_EINVAL, "a new leaf is neither kept, refined nor fused");
+  return 0;
+}
+
+int fr_tree_conn(int dim, int Dmax, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+                 int8_t* d_ftype, int8_t* d_slot, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n <= 0) return set_error(global_err(), FR_EINVAL, "bad size");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Err* err = global_err();
+  Alloc A{nullptr, s, err};
+  bool ok = false;
+  FR_TRY(tree_validate(dim, g, d_keys, n, 0, Dmax, &ok, A, s, err));
+  if (!ok) return set_error(err, FR_EINVAL, "input is not a complete sorted linear tree");
+  Scratch S(&A);
+  int32_t* bad = S.get<int32_t>(1);
+  if (!bad) return set_error(err, FR_ENOMEM, "conn scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  FR_TRY(tree_conn(dim, g, d_keys, n, d_nbr, d_ftype, d_slot, nullptr, bad, s, err));
+  int32_t hb = 0;
+  FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  if (hb) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced");
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// fr_internal.cuh -- internal declarations of the GB300 adaptive-FR library.
+// Key arithmetic (Sec. 2.2), device buffers, operator tables and the primitive entry points
+// (scan, radix sort, binary search) shared by the tree and solver translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fr.h"
+
+namespace frg {
+
+// ---------------------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------------------
+struct Err {
+  int code = 0;
+  std::string msg;
+};
+int set_error(Err* e, int code, const std::string& msg);
+Err* global_err();
+
+#define FR_TRY(expr)          \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != 0) return rc_; \
+  } while (0)
+
+#define FR_CUDA(err, expr)                                                                   \
+  do {                                                                                       \
+    cudaError_t ce_ = (expr);                                                                \
+    if (ce_ != cudaSuccess)                                                                  \
+      return ::frg::set_error((err), FR_ECUDA,                                               \
+                              std::string(#expr) + ": " + cudaGetErrorString(ce_));          \
+  } while (0)
+
+// every kernel launch is followed by this check, which also counts the launch
+int64_t& launch_counter();
+#define FR_LAUNCH_CHECK(err)            \
+  do {                                  \
+    ++::frg::launch_counter();          \
+    FR_CUDA(err, cudaGetLastError());   \
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Morton IDs (Sec. 2.2, Algorithm 1).  Bits are interleaved with the "magic number" bit spread
+// the paper mentions: spreading one coordinate's bits to every dim-th position by masked shifts.
+// The full-resolution interleave of an anchor whose low Dmax-D bits are zero equals the paper's
+// interleave of the depth-D coordinate followed by dim*(Dmax-D) zero bits.
+// ---------------------------------------------------------------------------------------------
+struct KeyGeo {
+  int dim, Dmax, mb;
+};
+
+inline int depth_bits(int Dmax) {
+  int mb = 0;
+  while ((1 << mb) < Dmax + 1) ++mb;
+  return mb;
+}
+
+__host__ __device__ __forceinline__ uint64_t spread2(uint64_t x) {
+  x &= 0xFFFFFFFFull;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  x = (x | (x << 1)) & 0x5555555555555555ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint64_t compact2(uint64_t x) {
+  x &= 0x5555555555555555ull;
+  x = (x ^ (x >> 1)) & 0x3333333333333333ull;
+  x = (x ^ (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x ^ (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x ^ (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x ^ (x >> 16)) & 0x00000000FFFFFFFFull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  x &= 0x1FFFFFull;
+  x = (x | (x << 32)) & 0x001F00000000FFFFull;
+  x = (x | (x << 16)) & 0x001F0000FF0000FFull;
+  x = (x | (x << 8)) & 0x100F00F00F00F00Full;
+  x = (x | (x << 4)) & 0x10C30C30C30C30C3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+__host__ __device__ __forceinline__ uint64_t compact3(uint64_t x) {
+  x &= 0x1249249249249249ull;
+  x = (x ^ (x >> 2)) & 0x10C30C30C30C30C3ull;
+  x = (x ^ (x >> 4)) & 0x100F00F00F00F00Full;
+  x = (x ^ (x >> 8)) & 0x001F0000FF0000FFull;
+  x = (x ^ (x >> 16)) & 0x001F00000000FFFFull;
+  x = (x ^ (x >> 32)) & 0x00000000001FFFFFull;
+  return x;
+}
+
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t interleave(const uint32_t* x) {
+  if (DIM == 2) return spread2(x[0]) | (spread2(x[1]) << 1);
+  return spread3(x[0]) | (spread3(x[1]) << 1) | (spread3(x[2]) << 2);
+}
+template <int DIM>
+__host__ __device__ __forceinline__ void deinterleave(uint64_t raw, uint32_t* x) {
+  if (DIM == 2) {
+    x[0] = uint32_t(compact2(raw));
+    x[1] = uint32_t(compact2(raw >> 1));
+  } else {
+    x[0] = uint32_t(compact3(raw));
+    x[1] = uint32_t(compact3(raw >> 1));
+    x[2] = uint32_t(compact3(raw >> 2));
+  }
+}
+
+// Device-side view of the key layout.
+struct KG {
+  int Dmax, mb;
+  __host__ __device__ __forceinline__ int depth(uint64_t k) const { return int(k & ((1ull << mb) - 1)); }
+  __host__ __device__ __forceinline__ uint64_t raw(uint64_t k) const { return k >> mb; }
+  __host__ __device__ __forceinline__ uint64_t make(uint64_t raw, int d) const { return (raw << mb) | uint64_t(d); }
+  __host__ __device__ __forceinline__ uint32_t width(int d) const { return 1u << (Dmax - d); }
+};
+
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t vol_raw(const KG& g, int d) {
+  return 1ull << (DIM * (g.Dmax - d));  // raw-ID span of one octant at depth d
+}
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t key_end(const KG& g, uint64_t k) {
+  // smallest key beyond the subtree of k (every descendant of k is below it)
+  return (g.raw(k) + vol_raw<DIM>(g, g.depth(k))) << g.mb;
+}
+template <int DIM>
+__host__ __device__ __forceinline__ bool is_ancestor(const KG& g, uint64_t a, uint64_t b) {
+  return b > a && b < key_end<DIM>(g, a);
+}
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t child_key(const KG& g, uint64_t k, int c) {
+  int d = g.depth(k);
+  return g.make(g.raw(k) + uint64_t(c) * vol_raw<DIM>(g, d + 1), d + 1);
+}
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t parent_key(const KG& g, uint64_t k) {
+  int d = g.depth(k);
+  uint64_t span = vol_raw<DIM>(g, d - 1);
+  return g.make(g.raw(k) / span * span, d - 1);
+}
+template <int DIM>
+__host__ __device__ __forceinline__ int child_index(const KG& g, uint64_t k) {
+  int d = g.depth(k);
+  return int((g.raw(k) >> (DIM * (g.Dmax - d))) & ((1u << DIM) - 1));
+}
+// key of the finest cell at integer point x (point location queries)
+template <int DIM>
+__host__ __device__ __forceinline__ uint64_t cell_key(const KG& g, const uint32_t* x) {
+  return g.make(interleave<DIM>(x), g.Dmax);
+}
+
+// first index in a[0..n) with a[i] >= v / > v
+__device__ __forceinline__ int64_t lower_bound_dev(const uint64_t* a, int64_t n, uint64_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t upper_bound_dev(const uint64_t* a, int64_t n, uint64_t v) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device memory: caller allocator or stream-ordered cudaMallocAsync.
+// ---------------------------------------------------------------------------------------------
+struct Alloc {
+  const fr_allocator* user = nullptr;
+  cudaStream_t stream = nullptr;
+  Err* err = nullptr;
+  void* get(size_t bytes);
+  void put(void* p);
+};
+
+template <class T>
+struct Buf {
+  T* p = nullptr;
+  size_t cap = 0;
+  // grows (never shrinks) to hold n elements; contents are not preserved
+  int ensure(Alloc& A, size_t n, double slack = 1.25) {
+    if (n <= cap && p) return 0;
+    if (p) A.put(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = size_t(double(n) * slack) + 16;
+    p = static_cast<T*>(A.get(want * sizeof(T)));
+    if (!p) return set_error(A.err, FR_ENOMEM, "device allocation failed");
+    cap = want;
+    return 0;
+  }
+  void release(Alloc& A) {
+    if (p) A.put(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+// scratch buffers released at scope exit (stream-ordered, so safe with pending kernels)
+struct Scratch {
+  Alloc* A;
+  std::vector<void*> ptrs;
+  explicit Scratch(Alloc* a) : A(a) {}
+  ~Scratch() {
+    for (void* p : ptrs) A->put(p);
+  }
+  template <class T>
+  T* get(size_t n) {
+    void* p = A->get((n ? n : 1) * sizeof(T));
+    if (p) ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+};
+
+// ---------------------------------------------------------------------------------------------
+// Primitives (fr_prim.cu)
+// ---------------------------------------------------------------------------------------------
+// exclusive scan of int32 counts into int64 offsets; the total goes to *d_total (device)
+int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                cudaStream_t s, Err* err);
+// ascending LSD radix sort of n keys over the low `bits` bits; d_tmp holds n keys of scratch
+int radix_sort_keys(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bits, Scratch& S,
+                    cudaStream_t s, Err* err);
+// reads a device int64 to the host (synchronises the stream)
+int read_i64(const int64_t* d, int64_t* h, cudaStream_t s, Err* err);
+
+// ---------------------------------------------------------------------------------------------
+// Tree pipeline (fr_tree.cu), on device arrays
+// ---------------------------------------------------------------------------------------------
+struct TreeOut {
+  Buf<uint64_t>* keys;  // output tree (grown as needed)
+  int64_t n;
+};
+int tree_encode(int dim, const KG& g, const int32_t* d_boxes, int64_t n, uint64_t* d_keys,
+                cudaStream_t s, Err* err);
+int tree_uniform(int dim, const KG& g, int D, uint64_t* d_keys, cudaStream_t s, Err* err);
+int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf<uint64_t>& out,
+                   int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
+int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
+              int64_t n, Buf<uint64_t>& out, int64_t* n_out, int64_t* n_ref, int64_t* n_coarse,
+              Alloc& A, cudaStream_t s, Err* err);
+// balances `keys` (n leaves) in place for depth passes D = Dmax .. Dlow
+int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n, int* passes,
+                 Alloc& A, cudaStream_t s, Err* err);
+int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
+             int64_t n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad, cudaStream_t s, Err* err);
+// connectivity; d_contrib (may be null) receives [n][2dim][4] coarse-side contributors
+int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+              int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
+              Err* err);
+// checks that keys are a complete sorted linear tree with depths in [Dlo, Dhi]
+int tree_validate(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
+                  bool* ok, Alloc& A, cudaStream_t s, Err* err);
+
+// ---------------------------------------------------------------------------------------------
+// FR operators (host-built, passed to kernels by value)
+// ---------------------------------------------------------------------------------------------
+constexpr int NPMAX = 5;
+struct DevOps {
+  double x[NPMAX], w[NPMAX];
+  double D[NPMAX][NPMAX];    // D[i][j] = l_j'(x_i)
+  double Dt[NPMAX][NPMAX];   // D folded with the correction: D - gL lm^T - gR lp^T
+  double lm[NPMAX], lp[NPMAX];
+  double gL[NPMAX], gR[NPMAX];
+  double I[2][NPMAX][NPMAX]; // I[h][i][j] = l_j((x_i + 2h - 1)/2): parent -> half h
+  double P[2][NPMAX][NPMAX]; // P[h][j][i] = (1/2)(w_i/w_j) I[h][i][j]: half h -> parent (L2)
+};
+int build_ops(int p, DevOps* o);
+
+struct DevProblem {
+  double L, gamma, rho_inf, p_inf, uinf[3];
+  int nvort;
+  double vort[16][4];
+};
+
+}  // namespace frg

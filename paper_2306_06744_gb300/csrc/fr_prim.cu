@@ -1,0 +1,250 @@
+// fr_prim.cu -- device-wide primitives without CUB: exclusive scan (reduce-then-scan, no
+// inter-block waits), stable LSD radix sort of uint64 keys (warp-match ranking), device memory.
+#include <cstdio>
+
+#include "fr_internal.cuh"
+
+namespace frg {
+
+// ---------------------------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------------------------
+int set_error(Err* e, int code, const std::string& msg) {
+  if (e) {
+    e->code = code;
+    e->msg = msg;
+  }
+  return code;
+}
+
+int64_t& launch_counter() {
+  static int64_t n = 0;
+  return n;
+}
+
+Err* global_err() {
+  static thread_local Err e;
+  return &e;
+}
+
+void* Alloc::get(size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (user && user->alloc) {
+    p = user->alloc(bytes, (void*)stream, user->ctx);
+  } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void Alloc::put(void* p) {
+  if (!p) return;
+  if (user && user->free)
+    user->free(p, (void*)stream, user->ctx);
+  else
+    cudaFreeAsync(p, stream);
+}
+
+int read_i64(const int64_t* d, int64_t* h, cudaStream_t s, Err* err) {
+  FR_CUDA(err, cudaMemcpyAsync(h, d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// exclusive scan: each block scans a tile of SCAN_T*SCAN_I items held blocked in registers,
+// block totals are scanned recursively, then added back.
+// ---------------------------------------------------------------------------------------------
+constexpr int SCAN_T = 256, SCAN_I = 8, SCAN_TILE = SCAN_T * SCAN_I;
+
+template <class TIn>
+__global__ void __launch_bounds__(SCAN_T) k_scan_tile(const TIn* __restrict__ in,
+                                                      int64_t* __restrict__ out, int64_t n,
+                                                      int64_t* __restrict__ sums) {
+  __shared__ int64_t s_warp[SCAN_T / 32];
+  __shared__ TIn s_in[SCAN_TILE];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int64_t base = int64_t(blockIdx.x) * SCAN_TILE;
+  for (int k = t; k < SCAN_TILE; k += SCAN_T) {  // coalesced load, then blocked use
+    int64_t idx = base + k;
+    s_in[k] = idx < n ? in[idx] : TIn(0);
+  }
+  __syncthreads();
+  int64_t v[SCAN_I], run = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_I; ++k) {
+    v[k] = run;
+    run += int64_t(s_in[t * SCAN_I + k]);
+  }
+  int64_t incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < SCAN_T / 32 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < SCAN_T / 32) s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  int64_t excl_thread = incl - run + (wid ? s_warp[wid - 1] : 0);
+  __syncthreads();
+  int64_t* s_out = reinterpret_cast<int64_t*>(s_in);  // reuse only if TIn is 8 bytes
+  if (sizeof(TIn) == 8) {
+#pragma unroll
+    for (int k = 0; k < SCAN_I; ++k) s_out[t * SCAN_I + k] = v[k] + excl_thread;
+    __syncthreads();
+    for (int k = t; k < SCAN_TILE; k += SCAN_T) {
+      int64_t idx = base + k;
+      if (idx < n) out[idx] = s_out[k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < SCAN_I; ++k) {
+      int64_t idx = base + t * SCAN_I + k;
+      if (idx < n) out[idx] = v[k] + excl_thread;
+    }
+  }
+  if (t == SCAN_T - 1) sums[blockIdx.x] = excl_thread + run;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += offs[i / SCAN_TILE];
+}
+
+template <class TIn>
+static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                     cudaStream_t s, Err* err) {
+  if (n <= 0) {
+    FR_CUDA(err, cudaMemsetAsync(d_total, 0, sizeof(int64_t), s));
+    return 0;
+  }
+  int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (nb == 1) {
+    k_scan_tile<TIn><<<1, SCAN_T, 0, s>>>(d_in, d_out, n, d_total);
+    FR_LAUNCH_CHECK(err);
+    return 0;
+  }
+  int64_t* sums = S.get<int64_t>(nb);
+  int64_t* offs = S.get<int64_t>(nb);
+  if (!sums || !offs) return set_error(err, FR_ENOMEM, "scan scratch");
+  k_scan_tile<TIn><<<unsigned(nb), SCAN_T, 0, s>>>(d_in, d_out, n, sums);
+  FR_LAUNCH_CHECK(err);
+  FR_TRY(scan_impl<int64_t>(sums, offs, nb, d_total, S, s, err));
+  k_scan_add<<<unsigned((n + 255) / 256), 256, 0, s>>>(d_out, n, offs);
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                cudaStream_t s, Err* err) {
+  return scan_impl<int32_t>(d_in, d_out, n, d_total, S, s, err);
+}
+
+// ---------------------------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits.  Pass = per-tile digit histogram -> exclusive scan of the
+// digit-major histogram -> stable scatter.  Inside a tile each warp ranks its contiguous chunk
+// round by round with __match_any_sync; per-warp digit counts give the cross-warp offsets.
+// ---------------------------------------------------------------------------------------------
+constexpr int RS_WARPS = 8, RS_T = RS_WARPS * 32, RS_ITEMS = 8;
+constexpr int RS_CHUNK = 32 * RS_ITEMS, RS_TILE = RS_WARPS * RS_CHUNK;
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                  int shift, int32_t* __restrict__ hist, int nb) {
+  __shared__ int32_t h[256];
+  const int t = threadIdx.x;
+  h[t] = 0;
+  __syncthreads();
+  const int64_t base = int64_t(blockIdx.x) * RS_TILE;
+  for (int k = t; k < RS_TILE; k += RS_T) {
+    int64_t idx = base + k;
+    if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  hist[int64_t(t) * nb + blockIdx.x] = h[t];
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t* __restrict__ in,
+                                                     uint64_t* __restrict__ out, int64_t n,
+                                                     int shift, const int64_t* __restrict__ offs,
+                                                     int nb) {
+  __shared__ int32_t wcnt[RS_WARPS][256];
+  __shared__ int64_t gofs[256];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int k = t; k < RS_WARPS * 256; k += RS_T) (&wcnt[0][0])[k] = 0;
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = int64_t(blockIdx.x) * RS_TILE + int64_t(w) * RS_CHUNK;
+  uint64_t key[RS_ITEMS];
+  int dig[RS_ITEMS], rank[RS_ITEMS];
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    int64_t idx = base + r * 32 + lane;
+    bool valid = idx < n;
+    key[r] = valid ? in[idx] : 0ull;
+    dig[r] = valid ? int((key[r] >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(0xffffffffu, dig[r]);
+    int before = valid ? wcnt[w][dig[r]] : 0;
+    rank[r] = before + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][dig[r]] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    int d = t;  // RS_T == 256: one digit per thread
+    int32_t run = 0;
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      int32_t c = wcnt[ww][d];
+      wcnt[ww][d] = run;
+      run += c;
+    }
+    gofs[d] = offs[int64_t(d) * nb + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    if (dig[r] < 256) out[gofs[dig[r]] + wcnt[w][dig[r]] + rank[r]] = key[r];
+  }
+}
+
+int radix_sort_keys(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bits, Scratch& S,
+                    cudaStream_t s, Err* err) {
+  if (n <= 1) return 0;
+  int64_t nb64 = (n + RS_TILE - 1) / RS_TILE;
+  if (nb64 > (int64_t(1) << 22)) return set_error(err, FR_EINVAL, "radix sort: too many keys");
+  int nb = int(nb64);
+  int32_t* hist = S.get<int32_t>(size_t(256) * nb);
+  int64_t* offs = S.get<int64_t>(size_t(256) * nb);
+  int64_t* total = S.get<int64_t>(1);
+  if (!hist || !offs || !total) return set_error(err, FR_ENOMEM, "radix sort scratch");
+  uint64_t* src = d_keys;
+  uint64_t* dst = d_tmp;
+  int passes = (bits + 7) / 8;
+  for (int ps = 0; ps < passes; ++ps) {
+    int shift = ps * 8;
+    k_rs_hist<<<nb, RS_T, 0, s>>>(src, n, shift, hist, nb);
+    FR_LAUNCH_CHECK(err);
+    FR_TRY(scan_counts(hist, offs, int64_t(256) * nb, total, S, s, err));
+    k_rs_scatter<<<nb, RS_T, 0, s>>>(src, dst, n, shift, offs, nb);
+    FR_LAUNCH_CHECK(err);
+    uint64_t* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  if (src != d_keys)
+    FR_CUDA(err, cudaMemcpyAsync(d_keys, src, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+  return 0;
+}
+
+}  // namespace frg

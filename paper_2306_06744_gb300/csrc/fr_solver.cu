@@ -1,0 +1,819 @@
+// fr_solver.cu -- flux reconstruction kernels for sm_103a (arXiv 2306.06744, Sec. 2.1 and 4.2-4.3):
+// closed-form vortex state, face traces, interface fluxes (Rusanov on conforming faces, mortar
+// projection at 2:1 hanging faces, owner-computes back-projection without atomics), the element
+// stage (corrected-flux divergence folded with the DG correction, SSP-RK3 combination, traces of
+// the new state), the adaptation indicator, solution transfer and deterministic norms.
+// All arithmetic is FP64.  Kernels are instantiated per (dim, p+1) so every small contraction is
+// fully unrolled.
+#include <cmath>
+
+#include "fr_internal.cuh"
+#include "fr_solver.cuh"
+
+namespace frg {
+
+// ---------------------------------------------------------------------------------------------
+// Host: 1D operators on Gauss-Legendre points.  Nodes from their closed forms (n <= 5), weights as
+// exact integrals of the Lagrange basis polynomials, barycentric Lagrange evaluation, and the DG
+// correction derivatives from the lift identity g_L'(x_i) = -l_i(-1)/w_i, g_R'(x_i) = l_i(1)/w_i
+// (Huynh's Radau correction recovers nodal DG, Sec. 2.1).
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+bool gl_nodes(int n, double* x) {
+  switch (n) {
+    case 2: {
+      double a = 1.0 / std::sqrt(3.0);
+      x[0] = -a; x[1] = a;
+      return true;
+    }
+    case 3: {
+      double a = std::sqrt(0.6);
+      x[0] = -a; x[1] = 0.0; x[2] = a;
+      return true;
+    }
+    case 4: {
+      double r = 2.0 / 7.0 * std::sqrt(1.2);
+      double a = std::sqrt(3.0 / 7.0 - r), b = std::sqrt(3.0 / 7.0 + r);
+      x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+      return true;
+    }
+    case 5: {
+      double r = 2.0 * std::sqrt(10.0 / 7.0);
+      double a = std::sqrt(5.0 - r) / 3.0, b = std::sqrt(5.0 + r) / 3.0;
+      x[0] = -b; x[1] = -a; x[2] = 0.0; x[3] = a; x[4] = b;
+      return true;
+    }
+    default: return false;
+  }
+}
+
+// barycentric weights lambda_j = 1 / prod_{k != j} (x_j - x_k)
+void bary(int n, const double* x, double* lam) {
+  for (int j = 0; j < n; ++j) {
+    double pr = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) pr *= (x[j] - x[k]);
+    lam[j] = 1.0 / pr;
+  }
+}
+
+// l_j(t) for all j (second barycentric form; exact nodes handled explicitly)
+void lag_all(int n, const double* x, const double* lam, double t, double* out) {
+  for (int j = 0; j < n; ++j)
+    if (t == x[j]) {
+      for (int k = 0; k < n; ++k) out[k] = (k == j) ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int j = 0; j < n; ++j) den += lam[j] / (t - x[j]);
+  for (int j = 0; j < n; ++j) out[j] = (lam[j] / (t - x[j])) / den;
+}
+
+// integral over [-1,1] of the j-th Lagrange polynomial, by expanding it in monomials
+double lag_integral(int n, const double* x, int j) {
+  double c[NPMAX + 1] = {1.0};  // coefficients of prod (t - x_k)/(x_j - x_k)
+  int deg = 0;
+  for (int k = 0; k < n; ++k) {
+    if (k == j) continue;
+    double s = 1.0 / (x[j] - x[k]);
+    double nc[NPMAX + 1] = {0};
+    for (int m = 0; m <= deg; ++m) {
+      nc[m + 1] += c[m] * s;
+      nc[m] -= c[m] * x[k] * s;
+    }
+    ++deg;
+    for (int m = 0; m <= deg; ++m) c[m] = nc[m];
+  }
+  double I = 0.0;
+  for (int m = 0; m <= deg; ++m)
+    if (m % 2 == 0) I += 2.0 * c[m] / double(m + 1);
+  return I;
+}
+
+}  // namespace
+
+int build_ops(int p, DevOps* o) {
+  int n = p + 1;
+  *o = DevOps{};
+  if (!gl_nodes(n, o->x)) return FR_EINVAL;
+  double lam[NPMAX];
+  bary(n, o->x, lam);
+  for (int j = 0; j < n; ++j) o->w[j] = lag_integral(n, o->x, j);
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      o->D[i][j] = (lam[j] / lam[i]) / (o->x[i] - o->x[j]);
+      s += o->D[i][j];
+    }
+    o->D[i][i] = -s;
+  }
+  lag_all(n, o->x, lam, -1.0, o->lm);
+  lag_all(n, o->x, lam, 1.0, o->lp);
+  for (int i = 0; i < n; ++i) {
+    o->gL[i] = -o->lm[i] / o->w[i];
+    o->gR[i] = o->lp[i] / o->w[i];
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) o->Dt[i][j] = o->D[i][j] - o->gL[i] * o->lm[j] - o->gR[i] * o->lp[j];
+  for (int h = 0; h < 2; ++h)
+    for (int i = 0; i < n; ++i) {
+      double row[NPMAX];
+      lag_all(n, o->x, lam, 0.5 * (o->x[i] + 2.0 * h - 1.0), row);
+      for (int j = 0; j < n; ++j) o->I[h][i][j] = row[j];
+    }
+  for (int h = 0; h < 2; ++h)
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i) o->P[h][j][i] = 0.5 * (o->w[i] / o->w[j]) * o->I[h][i][j];
+  return 0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+template <int DIM, int NP>
+struct Sz {
+  static constexpr int N = DIM == 2 ? NP * NP : NP * NP * NP;
+  static constexpr int NF = DIM == 2 ? NP : NP * NP;
+  static constexpr int NV = DIM + 2;
+  static constexpr int NFC = 2 * DIM;
+  static constexpr int NSUB = 1 << (DIM - 1);
+  static constexpr int EU = NV * N;        // doubles per element state
+  static constexpr int EF = NFC * NV * NF; // doubles per element face data
+  static constexpr int EPB = (128 / N) > 0 ? (128 / N) : 1;  // elements per 128-thread block
+};
+
+// element point index of position j along `axis` on the line through face point q
+template <int DIM, int NP>
+__device__ __forceinline__ int line_pt(int axis, int q, int j) {
+  if (DIM == 2) return axis == 0 ? j + NP * q : q + NP * j;
+  if (axis == 0) return j + NP * q;
+  if (axis == 1) return (q % NP) + NP * j + NP * NP * (q / NP);
+  return q + NP * NP * j;
+}
+// face point index on the face of `axis` for element point i, and i's position along the axis
+template <int DIM, int NP>
+__device__ __forceinline__ void pt_split(int i, int axis, int* q, int* ia) {
+  int ix = i % NP, iy = (i / NP) % NP, iz = DIM == 3 ? i / (NP * NP) : 0;
+  if (axis == 0) { *ia = ix; *q = DIM == 2 ? iy : iy + NP * iz; }
+  else if (axis == 1) { *ia = iy; *q = DIM == 2 ? ix : ix + NP * iz; }
+  else { *ia = iz; *q = ix + NP * iy; }
+}
+
+template <int DIM>
+__device__ __forceinline__ void rusanov(const double* qL, const double* qR, int axis, double gam,
+                                        double* F) {
+  constexpr int NV = DIM + 2;
+  double rL = 1.0 / qL[0], rR = 1.0 / qR[0];
+  double m2L = 0.0, m2R = 0.0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    m2L += qL[1 + b] * qL[1 + b];
+    m2R += qR[1 + b] * qR[1 + b];
+  }
+  double pL = (gam - 1.0) * (qL[NV - 1] - 0.5 * m2L * rL);
+  double pR = (gam - 1.0) * (qR[NV - 1] - 0.5 * m2R * rR);
+  double vL = qL[1 + axis] * rL, vR = qR[1 + axis] * rR;
+  double cL = sqrt(gam * pL * rL), cR = sqrt(gam * pR * rR);
+  double lam = fmax(fabs(vL) + cL, fabs(vR) + cR);
+  double fL[NV], fR[NV];
+  fL[0] = qL[1 + axis];
+  fR[0] = qR[1 + axis];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    fL[1 + b] = qL[1 + b] * vL + (b == axis ? pL : 0.0);
+    fR[1 + b] = qR[1 + b] * vR + (b == axis ? pR : 0.0);
+  }
+  fL[NV - 1] = (qL[NV - 1] + pL) * vL;
+  fR[NV - 1] = (qR[NV - 1] + pR) * vR;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (qR[v] - qL[v]);
+}
+
+// closed-form advected isentropic vortex (Sec. 5.2) at physical point X
+__device__ void vortex_state(const DevProblem& P, int dim, double t, const double* X, double* q) {
+  const double pi = 3.141592653589793238462643;
+  double du = 0.0, dv = 0.0, dT = 0.0;
+  for (int k = 0; k < P.nvort; ++k) {
+    double xc = P.vort[k][0] + P.uinf[0] * t, yc = P.vort[k][1] + P.uinf[1] * t;
+    double dx = X[0] - xc, dy = X[1] - yc;
+    dx -= P.L * floor(dx / P.L + 0.5);
+    dy -= P.L * floor(dy / P.L + 0.5);
+    double beta = P.vort[k][2], R = P.vort[k][3];
+    double r2 = (dx * dx + dy * dy) / (R * R);
+    double ex = exp(0.5 * (1.0 - r2));
+    du -= beta / (2.0 * pi) * (dy / R) * ex;
+    dv += beta / (2.0 * pi) * (dx / R) * ex;
+    dT -= (P.gamma - 1.0) * beta * beta / (8.0 * P.gamma * pi * pi) * exp(1.0 - r2);
+  }
+  double Tinf = P.p_inf / P.rho_inf;
+  double T = Tinf + dT;
+  double rho = P.rho_inf * pow(T / Tinf, 1.0 / (P.gamma - 1.0));
+  double p = rho * T;
+  double vel[3] = {P.uinf[0] + du, P.uinf[1] + dv, P.uinf[2]};
+  double ke = 0.0;
+  q[0] = rho;
+  for (int b = 0; b < dim; ++b) {
+    q[1 + b] = rho * vel[b];
+    ke += 0.5 * rho * vel[b] * vel[b];
+  }
+  q[1 + dim] = p / (P.gamma - 1.0) + ke;
+}
+
+template <int DIM, int NP>
+__device__ __forceinline__ void point_xyz(const KG& g, double L, uint64_t key, int i,
+                                          const DevOps& ops, double* X, double* h_out) {
+  uint32_t a[3] = {0, 0, 0};
+  deinterleave<DIM>(g.raw(key), a);
+  int d = g.depth(key);
+  double fine = L / double(1ull << g.Dmax);
+  double h = L / double(1ull << d);
+  int ii[3] = {i % NP, (i / NP) % NP, DIM == 3 ? i / (NP * NP) : 0};
+  X[2] = 0.0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) X[b] = double(a[b]) * fine + 0.5 * h * (ops.x[ii[b]] + 1.0);
+  *h_out = h;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------------------------
+template <int DIM, int NP>
+__global__ void k_exact(const uint64_t* __restrict__ keys, int64_t M, KG g, double t,
+                        const __grid_constant__ DevProblem P, const __grid_constant__ DevOps ops,
+                        double* __restrict__ u) {
+  using S = Sz<DIM, NP>;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * S::N) return;
+  int64_t e = idx / S::N;
+  int i = int(idx % S::N);
+  double X[3], h, q[5];
+  point_xyz<DIM, NP>(g, P.L, keys[e], i, ops, X, &h);
+  vortex_state(P, DIM, t, X, q);
+#pragma unroll
+  for (int v = 0; v < S::NV; ++v) u[(e * S::NV + v) * S::N + i] = q[v];
+}
+
+// traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
+template <int DIM, int NP>
+__global__ void k_traces(const double* __restrict__ u, int64_t M, const __grid_constant__ DevOps ops,
+                         double* __restrict__ tr) {
+  using S = Sz<DIM, NP>;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * S::EF) return;
+  int64_t e = idx / S::EF;
+  int r = int(idx % S::EF);
+  int f = r / (S::NV * S::NF), v = (r / S::NF) % S::NV, q = r % S::NF;
+  const double* lf = (f & 1) ? ops.lp : ops.lm;
+  const double* ue = u + (e * S::NV + v) * S::N;
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) s += lf[j] * ue[line_pt<DIM, NP>(f >> 1, q, j)];
+  tr[idx] = s;
+}
+
+// interface kernel: blocks [0, nb_conf) do conforming faces (one thread per face point),
+// the others do hanging faces (one block slice per coarse face: Rusanov on every mortar piece,
+// then the coarse side's L2 back-projection, Sec. 4.3).
+template <int DIM, int NP>
+__global__ void __launch_bounds__(128) k_faces(FaceArgs A, const __grid_constant__ DevOps ops) {
+  using S = Sz<DIM, NP>;
+  constexpr int NV = S::NV, NF = S::NF, NFC = S::NFC, NSUB = S::NSUB;
+  constexpr int PER = NSUB * NF;
+  constexpr int FPB = (128 / PER) > 0 ? 128 / PER : 1;
+  __shared__ double sF[FPB][NSUB][NV][NF];
+  const int tid = threadIdx.x;
+  if (int64_t(blockIdx.x) < A.nb_conf) {
+    int64_t idx = int64_t(blockIdx.x) * 128 + tid;
+    int64_t face = idx / NF;
+    int q = int(idx % NF);
+    if (face >= A.n_conf) return;
+    int32_t code = A.conf[face];
+    int64_t e = code >> 2;
+    int axis = code & 3;
+    int64_t nb = A.nbr[e * NFC + 2 * axis + 1];
+    double qL[NV], qR[NV], F[NV];
+    const double* tL = A.trace + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
+    const double* tR = A.trace + ((nb * NFC + 2 * axis) * NV) * NF + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      qL[v] = tL[v * NF];
+      qR[v] = tR[v * NF];
+    }
+    rusanov<DIM>(qL, qR, axis, A.gamma, F);
+    double* fL = A.fcomm + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
+    double* fR = A.fcomm + ((nb * NFC + 2 * axis) * NV) * NF + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fL[v * NF] = F[v];
+      fR[v * NF] = F[v];
+    }
+    return;
+  }
+  const int64_t hb = int64_t(blockIdx.x) - A.nb_conf;
+  const int lf = tid / PER, r = tid % PER, s = r / NF, q = r % NF;
+  const int64_t hf = hb * FPB + lf;
+  const bool act = lf < FPB && hf < A.n_hang;
+  int64_t ec = 0;
+  int fc = 0;
+  if (act) {
+    int32_t code = A.hang[hf];
+    ec = code >> 3;
+    fc = code & 7;
+    int axis = fc >> 1, sidec = fc & 1;
+    int64_t ek = A.contrib[hf * 4 + s];
+    int fk = fc ^ 1;
+    const double* tc = A.trace + ((ec * NFC + fc) * NV) * NF;
+    double uc[NV], uf[NV], F[NV];
+    const int q0 = q % NP, h0 = s & 1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+      if (DIM == 2) {
+#pragma unroll
+        for (int j0 = 0; j0 < NP; ++j0) acc += ops.I[h0][q0][j0] * tc[v * NF + j0];
+      } else {
+        const int q1 = q / NP, h1 = s >> 1;
+#pragma unroll
+        for (int j1 = 0; j1 < NP; ++j1) {
+          double a1 = 0.0;
+#pragma unroll
+          for (int j0 = 0; j0 < NP; ++j0) a1 += ops.I[h0][q0][j0] * tc[v * NF + j0 + NP * j1];
+          acc += ops.I[h1][q1][j1] * a1;
+        }
+      }
+      uc[v] = acc;
+      uf[v] = A.trace[((ek * NFC + fk) * NV + v) * NF + q];
+    }
+    if (sidec)
+      rusanov<DIM>(uc, uf, axis, A.gamma, F);
+    else
+      rusanov<DIM>(uf, uc, axis, A.gamma, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      A.fcomm[((ek * NFC + fk) * NV + v) * NF + q] = F[v];
+      sF[lf][s][v][q] = F[v];
+    }
+  }
+  __syncthreads();
+  if (act && s == 0) {
+    const int q0 = q % NP;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int sp = 0; sp < NSUB; ++sp) {
+        const int h0 = sp & 1;
+        if (DIM == 2) {
+#pragma unroll
+          for (int i0 = 0; i0 < NP; ++i0) acc += ops.P[h0][q0][i0] * sF[lf][sp][v][i0];
+        } else {
+          const int q1 = q / NP, h1 = sp >> 1;
+#pragma unroll
+          for (int i1 = 0; i1 < NP; ++i1) {
+            double a1 = 0.0;
+#pragma unroll
+            for (int i0 = 0; i0 < NP; ++i0) a1 += ops.P[h0][q0][i0] * sF[lf][sp][v][i0 + NP * i1];
+            acc += ops.P[h1][q1][i1] * a1;
+          }
+        }
+      }
+      A.fcomm[((ec * NFC + fc) * NV + v) * NF + q] = acc;
+    }
+  }
+}
+
+// element stage: R = -sum_a (2/h) [ sum_j Dt_ij f_j + gL_i F(-1) + gR_i F(+1) ] along each axis
+// (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt), then
+// out = a*un + b*us + c*R, and (optionally) the traces of out.
+template <int DIM, int NP>
+__global__ void __launch_bounds__(128) k_stage(StageArgs A, const __grid_constant__ DevOps ops) {
+  using S = Sz<DIM, NP>;
+  constexpr int N = S::N, NV = S::NV, NF = S::NF, NFC = S::NFC, EU = S::EU, EF = S::EF;
+  constexpr int EPB = S::EPB;
+  __shared__ double su[EPB * EU];
+  __shared__ double sfl[EPB * DIM * EU];
+  __shared__ double sfc[EPB * EF];
+  __shared__ double sh2[EPB];
+  const int tid = threadIdx.x;
+  const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
+  for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = A.us[e0 * EU + k];
+  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = A.fcomm[e0 * EF + k];
+  if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
+  __syncthreads();
+  const int le = tid / N, i = tid % N;
+  const bool act = le < ne;
+  double outv[NV];
+  if (act) {
+    const double* q = su + le * EU;
+    double rho = q[i], rinv = 1.0 / rho, E = q[(NV - 1) * N + i];
+    double vel[DIM], m2 = 0.0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      vel[b] = q[(1 + b) * N + i] * rinv;
+      m2 += q[(1 + b) * N + i] * vel[b];
+    }
+    double p = (A.gamma - 1.0) * (E - 0.5 * m2);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      double* fa = sfl + (le * DIM + a) * EU;
+      fa[i] = q[(1 + a) * N + i];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) fa[(1 + b) * N + i] = q[(1 + b) * N + i] * vel[a] + (a == b ? p : 0.0);
+      fa[(NV - 1) * N + i] = (E + p) * vel[a];
+    }
+  }
+  __syncthreads();
+  if (act) {
+    double R[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] = 0.0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      int qf, ia;
+      pt_split<DIM, NP>(i, a, &qf, &ia);
+      const double* fa = sfl + (le * DIM + a) * EU;
+      const double* Fm = sfc + le * EF + (2 * a) * NV * NF + qf;
+      const double* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double d = ops.gL[ia] * Fm[v * NF] + ops.gR[ia] * Fp[v * NF];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d += ops.Dt[ia][j] * fa[v * N + line_pt<DIM, NP>(a, qf, j)];
+        R[v] += d;
+      }
+    }
+    const double s2 = -sh2[le];
+    const int64_t base = (e0 + le) * EU + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double o = A.b * su[le * EU + v * N + i] + A.c * (s2 * R[v]);
+      if (A.a != 0.0) o += A.a * A.un[base + v * N];
+      outv[v] = o;
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) su[le * EU + v * N + i] = outv[v];
+  }
+  __syncthreads();
+  for (int k = tid; k < ne * EU; k += blockDim.x) A.out[e0 * EU + k] = su[k];
+  if (A.trace_out) {
+    for (int k = tid; k < ne * EF; k += blockDim.x) {
+      int le2 = k / EF, r = k % EF;
+      int f = r / (NV * NF), v = (r / NF) % NV, qq = r % NF;
+      const double* lf = (f & 1) ? ops.lp : ops.lm;
+      const double* ue = su + le2 * EU + v * N;
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s += lf[j] * ue[line_pt<DIM, NP>(f >> 1, qq, j)];
+      A.trace_out[e0 * EF + k] = s;
+    }
+  }
+}
+
+// Adaptation indicator, one thread per element.  Mode 0 (density gradient, a choice of this
+// library): eta = h max_i |grad rho(x_i)| with the uncorrected local derivative (2/h) D rho, so
+// eta = 2 max_i |D_xi rho|.  Mode 1 (analytic centre, Sec. 5.2): compare the numbers of points
+// closer than th_r and farther than th_c from the nearest vortex axis.
+template <int DIM, int NP>
+__global__ void k_indicator(const uint64_t* __restrict__ keys, int64_t M, KG g, int mode,
+                            double th_r, double th_c, double t, const __grid_constant__ DevProblem P,
+                            const __grid_constant__ DevOps ops, const double* __restrict__ u,
+                            int8_t* __restrict__ flags, double* __restrict__ eta) {
+  using S = Sz<DIM, NP>;
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  const double* rho = u + e * S::EU;
+  int8_t f = 0;
+  double val = 0.0;
+  if (mode == 0) {
+    double gmax = 0.0;
+    for (int i = 0; i < S::N; ++i) {
+      double g2 = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        int qf, ia;
+        pt_split<DIM, NP>(i, a, &qf, &ia);
+        double d = 0.0;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d += ops.D[ia][j] * __ldg(rho + line_pt<DIM, NP>(a, qf, j));
+        g2 += d * d;
+      }
+      gmax = fmax(gmax, g2);
+    }
+    val = 2.0 * sqrt(gmax);
+    f = val > th_r ? 1 : (val < th_c ? -1 : 0);
+  } else {
+    int nin = 0, nout = 0;
+    uint64_t key = keys[e];
+    for (int i = 0; i < S::N; ++i) {
+      double X[3], h;
+      point_xyz<DIM, NP>(g, P.L, key, i, ops, X, &h);
+      double rmin = 1e300;
+      for (int k = 0; k < P.nvort; ++k) {
+        double dx = X[0] - (P.vort[k][0] + P.uinf[0] * t), dy = X[1] - (P.vort[k][1] + P.uinf[1] * t);
+        dx -= P.L * floor(dx / P.L + 0.5);
+        dy -= P.L * floor(dy / P.L + 0.5);
+        rmin = fmin(rmin, sqrt(dx * dx + dy * dy));
+      }
+      nin += rmin < th_r;
+      nout += rmin > th_c;
+    }
+    val = double(nin - nout);
+    f = nin > nout ? 1 : (nin < nout ? -1 : 0);
+  }
+  flags[e] = f;
+  if (eta) eta[e] = val;
+}
+
+// Solution transfer (Sec. 4.2): copy; interpolation of the old (ancestor) polynomial at the new
+// points, with the Lagrange weights evaluated in the kernel; L2 projection of 2^dim fused
+// children with the tensor-product operators P (exact-quadrature mass and cross-mass matrices).
+template <int DIM, int NP>
+__global__ void k_transfer(KG g, const uint64_t* __restrict__ old_keys,
+                           const uint64_t* __restrict__ new_keys, const int32_t* __restrict__ src,
+                           const int8_t* __restrict__ tag, int64_t Mn,
+                           const __grid_constant__ DevOps ops, const double* __restrict__ uo,
+                           double* __restrict__ un) {
+  using S = Sz<DIM, NP>;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= Mn * S::N) return;
+  int64_t j = idx / S::N;
+  int i = int(idx % S::N);
+  int64_t sidx = src[j];
+  int tg = tag[j];
+  int ii[3] = {i % NP, (i / NP) % NP, DIM == 3 ? i / (NP * NP) : 0};
+  if (tg == 0) {
+#pragma unroll
+    for (int v = 0; v < S::NV; ++v) un[(j * S::NV + v) * S::N + i] = uo[(sidx * S::NV + v) * S::N + i];
+  } else if (tg == 1) {
+    uint64_t kA = old_keys[sidx], kK = new_keys[j];
+    uint32_t xa[3] = {0, 0, 0}, xk[3] = {0, 0, 0};
+    deinterleave<DIM>(g.raw(kA), xa);
+    deinterleave<DIM>(g.raw(kK), xk);
+    double wA = double(g.width(g.depth(kA))), wK = double(g.width(g.depth(kK)));
+    double lw[DIM][NP];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      double xi = -1.0 + 2.0 * (double(xk[a] - xa[a]) + 0.5 * (ops.x[ii[a]] + 1.0) * wK) / wA;
+#pragma unroll
+      for (int m = 0; m < NP; ++m) {
+        double pr = 1.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+          if (k != m) pr *= (xi - ops.x[k]) / (ops.x[m] - ops.x[k]);
+        lw[a][m] = pr;
+      }
+    }
+    for (int v = 0; v < S::NV; ++v) {
+      const double* ua = uo + (sidx * S::NV + v) * S::N;
+      double acc = 0.0;
+      for (int q = 0; q < S::N; ++q) {
+        double wq = lw[0][q % NP] * lw[1][(q / NP) % NP];
+        if (DIM == 3) wq *= lw[DIM - 1][q / (NP * NP)];
+        acc += wq * ua[q];
+      }
+      un[(j * S::NV + v) * S::N + i] = acc;
+    }
+  } else {
+    for (int v = 0; v < S::NV; ++v) {
+      double acc = 0.0;
+      for (int c = 0; c < (1 << DIM); ++c) {
+        const double* uc = uo + ((sidx + c) * S::NV + v) * S::N;
+        int h0 = c & 1, h1 = (c >> 1) & 1, h2 = (c >> 2) & 1;
+        for (int q = 0; q < S::N; ++q) {
+          int q0 = q % NP, q1 = (q / NP) % NP, q2 = DIM == 3 ? q / (NP * NP) : 0;
+          double wq = ops.P[h0][ii[0]][q0] * ops.P[h1][ii[1]][q1];
+          if (DIM == 3) wq *= ops.P[h2][ii[2]][q2];
+          acc += wq * uc[q];
+        }
+      }
+      un[(j * S::NV + v) * S::N + i] = acc;
+    }
+  }
+}
+
+// Norms: per-element sums, block tree reduction in fixed order, then one block over the partials.
+constexpr int NRM_T = 128, NRM_W = 8;
+template <int DIM, int NP>
+__global__ void __launch_bounds__(NRM_T) k_norms(const uint64_t* __restrict__ keys, int64_t M, KG g,
+                                                 double t, const __grid_constant__ DevProblem P,
+                                                 const __grid_constant__ DevOps ops,
+                                                 const double* __restrict__ u,
+                                                 double* __restrict__ partial) {
+  using S = Sz<DIM, NP>;
+  __shared__ double sm[NRM_W][NRM_T];
+  int64_t e = int64_t(blockIdx.x) * NRM_T + threadIdx.x;
+  double acc[NRM_W];
+  for (int k = 0; k < NRM_W; ++k) acc[k] = 0.0;
+  acc[S::NV + 1] = 1e300;
+  acc[S::NV + 2] = 1e300;
+  if (e < M) {
+    uint64_t key = keys[e];
+    for (int i = 0; i < S::N; ++i) {
+      double X[3], h, qe[5], q[5];
+      point_xyz<DIM, NP>(g, P.L, key, i, ops, X, &h);
+      vortex_state(P, DIM, t, X, qe);
+      double Wt = ops.w[i % NP] * ops.w[(i / NP) % NP];
+      if (DIM == 3) Wt *= ops.w[i / (NP * NP)];
+      double J = 0.5 * h * 0.5 * h;
+      if (DIM == 3) J *= 0.5 * h;
+#pragma unroll
+      for (int v = 0; v < S::NV; ++v) q[v] = u[(e * S::NV + v) * S::N + i];
+      double d = qe[0] - q[0];
+      acc[0] += Wt * J * d * d;
+#pragma unroll
+      for (int v = 0; v < S::NV; ++v) acc[1 + v] += Wt * J * q[v];
+      double m2 = 0.0;
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) m2 += q[1 + b] * q[1 + b];
+      double p = (P.gamma - 1.0) * (q[S::NV - 1] - 0.5 * m2 / q[0]);
+      acc[S::NV + 1] = fmin(acc[S::NV + 1], q[0]);
+      acc[S::NV + 2] = fmin(acc[S::NV + 2], p);
+    }
+  }
+  for (int k = 0; k < NRM_W; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = NRM_T / 2; st > 0; st >>= 1) {
+    if (int(threadIdx.x) < st)
+      for (int k = 0; k < NRM_W; ++k) {
+        double a = sm[k][threadIdx.x], b = sm[k][threadIdx.x + st];
+        sm[k][threadIdx.x] = (k == S::NV + 1 || k == S::NV + 2) ? fmin(a, b) : a + b;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < NRM_W) partial[int64_t(blockIdx.x) * NRM_W + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(NRM_T) k_norms_final(const double* __restrict__ partial,
+                                                       int64_t nb, int nv, double* __restrict__ out) {
+  __shared__ double sm[NRM_W][NRM_T];
+  double acc[NRM_W];
+  for (int k = 0; k < NRM_W; ++k) acc[k] = (k == nv + 1 || k == nv + 2) ? 1e300 : 0.0;
+  for (int64_t b = threadIdx.x; b < nb; b += NRM_T)
+    for (int k = 0; k < NRM_W; ++k) {
+      double x = partial[b * NRM_W + k];
+      acc[k] = (k == nv + 1 || k == nv + 2) ? fmin(acc[k], x) : acc[k] + x;
+    }
+  for (int k = 0; k < NRM_W; ++k) sm[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int st = NRM_T / 2; st > 0; st >>= 1) {
+    if (int(threadIdx.x) < st)
+      for (int k = 0; k < NRM_W; ++k) {
+        double a = sm[k][threadIdx.x], b = sm[k][threadIdx.x + st];
+        sm[k][threadIdx.x] = (k == nv + 1 || k == nv + 2) ? fmin(a, b) : a + b;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < NRM_W) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+template <int DIM, int NP>
+__global__ void k_maxspeed(const double* __restrict__ u, int64_t M, double gam,
+                           unsigned long long* dmax) {
+  using S = Sz<DIM, NP>;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * S::N) return;
+  int64_t e = idx / S::N;
+  int i = int(idx % S::N);
+  const double* q = u + e * S::EU + i;
+  double rho = q[0], m2 = 0.0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) m2 += q[(1 + b) * S::N] * q[(1 + b) * S::N];
+  double p = (gam - 1.0) * (q[(S::NV - 1) * S::N] - 0.5 * m2 / rho);
+  double s = sqrt(m2) / rho + sqrt(gam * p / rho);
+  if (s > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(s));
+}
+
+inline unsigned nb_of(int64_t n, int b) { return unsigned((n + b - 1) / b); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// Launchers: dispatch on (dim, p+1)
+// ---------------------------------------------------------------------------------------------
+#define FR_DISPATCH(dim, p, ...)                                        \
+  do {                                                                  \
+    int np_ = (p) + 1;                                                  \
+    if ((dim) == 2) {                                                   \
+      constexpr int DD = 2;                                             \
+      if (np_ == 2) { constexpr int NN = 2; __VA_ARGS__; }              \
+      else if (np_ == 3) { constexpr int NN = 3; __VA_ARGS__; }         \
+      else if (np_ == 4) { constexpr int NN = 4; __VA_ARGS__; }         \
+      else if (np_ == 5) { constexpr int NN = 5; __VA_ARGS__; }         \
+      else return set_error(err, FR_EINVAL, "p out of range");        \
+    } else if ((dim) == 3) {                                            \
+      constexpr int DD = 3;                                             \
+      if (np_ == 2) { constexpr int NN = 2; __VA_ARGS__; }              \
+      else if (np_ == 3) { constexpr int NN = 3; __VA_ARGS__; }         \
+      else if (np_ == 4) { constexpr int NN = 4; __VA_ARGS__; }         \
+      else if (np_ == 5) { constexpr int NN = 5; __VA_ARGS__; }         \
+      else return set_error(err, FR_EINVAL, "p out of range");        \
+    } else {                                                            \
+      return set_error(err, FR_EINVAL, "dim out of range");           \
+    }                                                                   \
+  } while (0)
+
+static int ipow(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
+                 const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err) {
+  if (M <= 0) return 0;
+  int64_t T = M * ipow(p + 1, dim);
+  FR_DISPATCH(dim, p, (k_exact<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(keys, M, g, t, P, ops, u)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_traces(int dim, int p, const double* u, int64_t M, const DevOps& ops, double* tr,
+                  cudaStream_t s, Err* err) {
+  if (M <= 0) return 0;
+  int64_t T = M * 2 * dim * (dim + 2) * ipow(p + 1, dim - 1);
+  FR_DISPATCH(dim, p, (k_traces<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(u, M, ops, tr)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_faces(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {
+  int NF = ipow(p + 1, dim - 1), PER = (1 << (dim - 1)) * NF;
+  int FPB = 128 / PER > 0 ? 128 / PER : 1;
+  A.nb_conf = (A.n_conf * NF + 127) / 128;
+  int64_t nb_hang = (A.n_hang + FPB - 1) / FPB;
+  int64_t nb = A.nb_conf + nb_hang;
+  if (nb == 0) return 0;
+  FR_DISPATCH(dim, p, (k_faces<DD, NN><<<unsigned(nb), 128, 0, s>>>(A, ops)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_stage(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, Err* err) {
+  if (A.M <= 0) return 0;
+  FR_DISPATCH(dim, p, ({
+                using SS = Sz<DD, NN>;
+                k_stage<DD, NN><<<nb_of(A.M, SS::EPB), 128, 0, s>>>(A, ops);
+              }));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double t,
+                     const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
+                     const DevOps& ops, const double* u, int8_t* flags, double* eta,
+                     cudaStream_t s, Err* err) {
+  if (M <= 0) return 0;
+  FR_DISPATCH(dim, p, (k_indicator<DD, NN><<<nb_of(M, 128), 128, 0, s>>>(keys, M, g, mode, th_r, th_c, t, P, ops, u, flags, eta)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
+                    const int32_t* src, const int8_t* tag, int64_t M_new, const DevOps& ops,
+                    const double* u_old, double* u_new, cudaStream_t s, Err* err) {
+  if (M_new <= 0) return 0;
+  int64_t T = M_new * ipow(p + 1, dim);
+  FR_DISPATCH(dim, p, (k_transfer<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(g, old_keys, new_keys, src, tag, M_new, ops, u_old, u_new)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int norms_blocks(int dim, int p, int64_t M) {
+  (void)dim;
+  (void)p;
+  return int((M + NRM_T - 1) / NRM_T);
+}
+
+int launch_norms(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
+                 const DevProblem& P, const DevOps& ops, const double* u, double* d_partial,
+                 int64_t nblocks_cap, double* d_out, cudaStream_t s, Err* err) {
+  int64_t nb = (M + NRM_T - 1) / NRM_T;
+  if (nb > nblocks_cap) return set_error(err, FR_EINVAL, "norms scratch too small");
+  if (nb > 0) {
+    FR_DISPATCH(dim, p, (k_norms<DD, NN><<<unsigned(nb), NRM_T, 0, s>>>(keys, M, g, t, P, ops, u, d_partial)));
+    FR_LAUNCH_CHECK(err);
+  }
+  k_norms_final<<<1, NRM_T, 0, s>>>(d_partial, nb, dim + 2, d_out);
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int launch_maxspeed(int dim, int p, const double* u, int64_t M, double gamma,
+                    unsigned long long* d_max, cudaStream_t s, Err* err) {
+  FR_CUDA(err, cudaMemsetAsync(d_max, 0, sizeof(unsigned long long), s));
+  if (M <= 0) return 0;
+  int64_t T = M * ipow(p + 1, dim);
+  FR_DISPATCH(dim, p, (k_maxspeed<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(u, M, gamma, d_max)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+}  // namespace frg

@@ -1,0 +1,55 @@
+// fr_solver.cuh -- launch interface of the FR kernels (fr_solver.cu).
+#pragma once
+#include "fr_internal.cuh"
+
+namespace frg {
+
+struct FaceArgs {
+  const double* trace;    // [M][2dim][nv][Nf] traces of the current stage state
+  double* fcomm;          // [M][2dim][nv][Nf] common flux along +axis
+  const int32_t* nbr;     // [M][2dim]
+  const int32_t* conf;    // conforming faces: (minus element << 2) | axis
+  const int32_t* hang;    // hanging faces: (coarse element << 3) | coarse face
+  const int32_t* contrib; // [n_hang][4] fine elements in slot order
+  int64_t n_conf, n_hang, nb_conf;
+  double gamma;
+};
+
+struct StageArgs {
+  const uint64_t* keys;
+  const double* us;     // stage state
+  const double* un;     // state at the start of the step (read only when a != 0)
+  const double* fcomm;
+  double* out;          // a*un + b*us + c*R (may alias us or un element-wise)
+  double* trace_out;    // traces of out, or null
+  int64_t M;
+  KG g;
+  double L, gamma, a, b, c;
+};
+
+struct Mesh;  // defined in fr_api.cu
+
+int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
+                 const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err);
+int launch_traces(int dim, int p, const double* u, int64_t M, const DevOps& ops, double* tr,
+                  cudaStream_t s, Err* err);
+int launch_faces(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
+int launch_stage(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, Err* err);
+// indicator: mode 0 density gradient, 1 analytic centre; flags int8[M], eta double[M] (nullable)
+int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double t,
+                     const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
+                     const DevOps& ops, const double* u, int8_t* flags, double* eta,
+                     cudaStream_t s, Err* err);
+int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
+                    const int32_t* src, const int8_t* tag, int64_t M_new, const DevOps& ops,
+                    const double* u_old, double* u_new, cudaStream_t s, Err* err);
+// norms: out[0] = sum w|J|(rho_ex-rho)^2, out[1..nv] integrals, out[nv+1] min rho, out[nv+2] min p
+int launch_norms(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
+                 const DevProblem& P, const DevOps& ops, const double* u, double* d_partial,
+                 int64_t nblocks_cap, double* d_out, cudaStream_t s, Err* err);
+int norms_blocks(int dim, int p, int64_t M);
+// largest |v|+c over all points, written to *d_max (as the bit pattern of a positive double)
+int launch_maxspeed(int dim, int p, const double* u, int64_t M, double gamma,
+                    unsigned long long* d_max, cudaStream_t s, Err* err);
+
+}  // namespace frg

@@ -1,0 +1,495 @@
+// fr_tree.cu -- linear-tree kernels (Sec. 3 and Sec. 4.1-4.2 of arXiv 2306.06744) on sm_103a:
+// Morton encoding, linearisation, the adaptation edit, 2:1 balance by depth passes, old->new
+// mapping and face connectivity.  Every generating step is count -> exclusive scan -> write at
+// the scanned position, so outputs are deterministic and already in Morton order (no atomic
+// counters, no retry on shared-memory overflow).
+#include "fr_internal.cuh"
+
+namespace frg {
+
+namespace {
+
+constexpr int TB = 256;
+inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); }
+
+template <int DIM>
+__global__ void k_encode(const int32_t* __restrict__ boxes, int64_t n, uint64_t* __restrict__ keys,
+                         KG g, int32_t* bad) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int d = boxes[4 * i];
+  uint32_t x[3];
+  bool ok = d >= 0 && d <= g.Dmax;
+  for (int a = 0; a < DIM; ++a) {
+    int32_t v = boxes[4 * i + 1 + a];
+    ok = ok && v >= 0 && int64_t(v) < (int64_t(1) << g.Dmax);
+    x[a] = uint32_t(v);
+    if (ok) ok = (x[a] & (g.width(d) - 1u)) == 0u;
+  }
+  if (!ok) {
+    atomicExch(bad, 1);
+    keys[i] = 0;
+    return;
+  }
+  keys[i] = g.make(interleave<DIM>(x), d);
+}
+
+template <int DIM>
+__global__ void k_uniform(uint64_t* __restrict__ keys, int64_t count, KG g, int D) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < count) keys[i] = g.make(uint64_t(i) << (DIM * (g.Dmax - D)), D);
+}
+
+// keep[i] = no duplicate of and no descendant in the next key (sorted input: the subtree of an
+// octant follows it contiguously, so checking the successor suffices)
+template <int DIM>
+__global__ void k_lin_count(const uint64_t* __restrict__ k, int64_t n, KG g, int32_t* __restrict__ cnt) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool drop = false;
+  if (i + 1 < n) {
+    uint64_t a = k[i], b = k[i + 1];
+    drop = (a == b) || is_ancestor<DIM>(g, a, b);
+  }
+  cnt[i] = drop ? 0 : 1;
+}
+
+__global__ void k_compact(const uint64_t* __restrict__ k, const int32_t* __restrict__ cnt,
+                          const int64_t* __restrict__ offs, int64_t n, uint64_t* __restrict__ out) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n && cnt[i]) out[offs[i]] = k[i];
+}
+
+// Adaptation edit (Sec. 4.1): action 0 keep, 1 refine, 2 head of a coarsened sibling group
+// (becomes the parent), 3 other member of that group (removed).  Coarsening needs all 2^dim
+// siblings present as consecutive leaves (raw IDs consecutive, Sec. 4.1) and all flagged -1.
+template <int DIM>
+__global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __restrict__ flags,
+                             int64_t n, KG g, int Dbase, int8_t* __restrict__ act,
+                             int32_t* __restrict__ cnt) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NC = 1 << DIM;
+  uint64_t key = k[i];
+  int d = g.depth(key);
+  int f = flags[i];
+  int a = 0;
+  if (f > 0 && d < g.Dmax) {
+    a = 1;
+  } else if (f < 0 && d > Dbase) {
+    int c = child_index<DIM>(g, key);
+    int64_t h = i - c;
+    bool ok = h >= 0 && h + NC <= n;
+    if (ok) {
+      uint64_t par = parent_key<DIM>(g, key);
+      for (int s = 0; s < NC && ok; ++s)
+        ok = k[h + s] == child_key<DIM>(g, par, s) && flags[h + s] < 0;
+    }
+    if (ok) a = (c == 0) ? 2 : 3;
+  }
+  act[i] = int8_t(a);
+  cnt[i] = a == 1 ? NC : (a == 3 ? 0 : 1);
+}
+
+template <int DIM>
+__global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __restrict__ act,
+                             const int64_t* __restrict__ offs, int64_t n, KG g,
+                             uint64_t* __restrict__ out, unsigned long long* stats) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key = k[i];
+  int64_t o = offs[i];
+  switch (act[i]) {
+    case 0: out[o] = key; break;
+    case 1:
+      for (int c = 0; c < (1 << DIM); ++c) out[o + c] = child_key<DIM>(g, key, c);
+      atomicAdd(&stats[0], 1ull);
+      break;
+    case 2:
+      out[o] = parent_key<DIM>(g, key);
+      atomicAdd(&stats[1], 1ull);
+      break;
+    default: break;
+  }
+}
+
+// 2:1 balance pass at depth D (Sec. 3.2, balance algorithm): every depth-D leaf looks up the
+// leaf containing the anchor of each of its 3^dim-1 same-size neighbour boxes (periodic).  A
+// containing leaf A coarser than D-1 is split along the path towards that box down to depth D-1;
+// all 2^dim children of every level on the path are emitted.
+template <int DIM>
+struct Nofs {
+  static constexpr int value = DIM == 2 ? 8 : 26;
+};
+
+template <int DIM>
+__device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_t n, const KG& g,
+                                          int D, int64_t i, int o, uint32_t* N, int* dA) {
+  uint64_t key = k[i];
+  if (g.depth(key) != D) return false;
+  int oo = o < (DIM == 2 ? 4 : 13) ? o : o + 1;  // skip the centre of the 3^dim stencil
+  uint32_t x[3];
+  deinterleave<DIM>(g.raw(key), x);
+  uint32_t w = g.width(D), mask = (g.Dmax >= 32) ? 0xFFFFFFFFu : ((1u << g.Dmax) - 1u);
+  for (int a = 0; a < DIM; ++a) {
+    int off = (oo / (a == 0 ? 1 : (a == 1 ? 3 : 9))) % 3 - 1;
+    N[a] = (x[a] + uint32_t(off) * w) & mask;  // periodic wrap on the 2^Dmax grid
+  }
+  int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
+  if (j < 0) j = 0;  // only on an incomplete tree, which callers reject beforehand
+  *dA = g.depth(k[j]);
+  return *dA < D - 1;
+}
+
+template <int DIM>
+__global__ void k_bal_count(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
+                            int32_t* __restrict__ cnt) {
+  constexpr int NO = Nofs<DIM>::value;
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * NO) return;
+  uint32_t N[3];
+  int dA;
+  bool need = bal_query<DIM>(k, n, g, D, t / NO, int(t % NO), N, &dA);
+  cnt[t] = need ? (D - 1 - dA) << DIM : 0;
+}
+
+template <int DIM>
+__global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
+                          const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
+  constexpr int NO = Nofs<DIM>::value;
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * NO) return;
+  uint32_t N[3];
+  int dA;
+  if (!bal_query<DIM>(k, n, g, D, t / NO, int(t % NO), N, &dA)) return;
+  int64_t o = offs[t];
+  uint64_t rawN = interleave<DIM>(N);
+  for (int l = dA + 1; l <= D - 1; ++l) {
+    uint64_t span = vol_raw<DIM>(g, l - 1);
+    uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
+    for (int c = 0; c < (1 << DIM); ++c) out[o++] = child_key<DIM>(g, anc, c);
+  }
+}
+
+// replace every leaf by the linearised generated octants inside it (or keep it)
+template <int DIM>
+__global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t n,
+                              const uint64_t* __restrict__ S, int64_t nS, KG g,
+                              int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key = k[i];
+  int64_t lo = lower_bound_dev(S, nS, key);
+  int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
+  cnt[i] = hi > lo ? int32_t(hi - lo) : 1;
+  lo_out[i] = hi > lo ? lo : -1;  // -1: the leaf is kept as it is
+}
+
+__global__ void k_merge_write(const uint64_t* __restrict__ k, int64_t n,
+                              const uint64_t* __restrict__ S, const int32_t* __restrict__ cnt,
+                              const int64_t* __restrict__ lo, const int64_t* __restrict__ offs,
+                              uint64_t* __restrict__ out) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int64_t o = offs[i], l = lo[i];
+  if (l < 0) {
+    out[o] = k[i];
+  } else {
+    int c = cnt[i];
+    for (int r = 0; r < c; ++r) out[o + r] = S[l + r];
+  }
+}
+
+// Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
+template <int DIM>
+__global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64_t* __restrict__ nw,
+                      int64_t nn, KG g, int32_t* __restrict__ src, int8_t* __restrict__ tag,
+                      int32_t* bad) {
+  int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (j >= nn) return;
+  uint64_t key = nw[j];
+  int64_t B = lower_bound_dev(old, no, key);
+  if (B < no && old[B] == key) {
+    src[j] = int32_t(B);
+    tag[j] = 0;
+  } else if (B > 0 && is_ancestor<DIM>(g, old[B - 1], key)) {
+    src[j] = int32_t(B - 1);
+    tag[j] = 1;
+  } else {
+    // the old leaves must be exactly the 2^dim children of the new leaf; otherwise the tree
+    // pair is invalid: report it and emit an in-bounds copy so later kernels stay in bounds
+    bool ok = B + (1 << DIM) <= no;
+    for (int c = 0; c < (1 << DIM) && ok; ++c) ok = old[B + c] == child_key<DIM>(g, key, c);
+    if (ok) {
+      src[j] = int32_t(B);
+      tag[j] = 2;
+    } else {
+      atomicExch(bad, 1);
+      src[j] = int32_t(B < no ? B : no - 1);
+      tag[j] = 0;
+    }
+  }
+}
+
+// Face connectivity (Sec. 3.3): same-depth face-neighbour box, point location of its anchor.
+template <int DIM>
+__global__ void k_conn(const uint64_t* __restrict__ k, int64_t n, KG g, int32_t* __restrict__ nbr,
+                       int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
+                       int32_t* __restrict__ contrib, int32_t* bad) {
+  constexpr int NFC = 2 * DIM;
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n * NFC) return;
+  int64_t e = t / NFC;
+  int f = int(t % NFC), axis = f >> 1, side = f & 1;
+  uint64_t key = k[e];
+  int d = g.depth(key);
+  uint32_t x[3], N[3];
+  deinterleave<DIM>(g.raw(key), x);
+  uint32_t w = g.width(d), mask = (g.Dmax >= 32) ? 0xFFFFFFFFu : ((1u << g.Dmax) - 1u);
+  for (int a = 0; a < DIM; ++a) N[a] = x[a];
+  N[axis] = (x[axis] + (side ? w : (0u - w))) & mask;
+  uint64_t kN = g.make(interleave<DIM>(N), d);
+  int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
+  if (j < 0) j = 0;
+  uint64_t kj = k[j];
+  int dj = g.depth(kj);
+  if (kj == kN) {
+    nbr[t] = int32_t(j);
+    ftype[t] = 0;
+    slot[t] = -1;
+  } else if (dj < d) {
+    if (dj != d - 1) atomicExch(bad, 1);
+    nbr[t] = int32_t(j);
+    ftype[t] = 1;
+    int c = child_index<DIM>(g, key), s = 0, sh = 0;
+    for (int b = 0; b < DIM; ++b)
+      if (b != axis) s |= ((c >> b) & 1) << sh++;
+    slot[t] = int8_t(s);
+  } else {
+    ftype[t] = 2;
+    slot[t] = 0;
+    int first = -1;
+    for (int c = 0; c < (1 << DIM); ++c) {
+      if (((c >> axis) & 1) != (side ? 0 : 1)) continue;
+      uint64_t kc = child_key<DIM>(g, kN, c);
+      int64_t m = lower_bound_dev(k, n, kc);
+      if (m >= n || k[m] != kc) {
+        atomicExch(bad, 1);
+        m = 0;
+      }
+      int s = 0, sh = 0;
+      for (int b = 0; b < DIM; ++b)
+        if (b != axis) s |= ((c >> b) & 1) << sh++;
+      if (s == 0) first = int(m);
+      if (contrib) contrib[t * 4 + s] = int32_t(m);
+    }
+    nbr[t] = first;
+  }
+}
+
+template <int DIM>
+__global__ void k_validate(const uint64_t* __restrict__ k, int64_t n, KG g, int Dlo, int Dhi,
+                           int32_t* bad) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint64_t key = k[i];
+  int d = g.depth(key);
+  uint64_t total = 1ull << (DIM * g.Dmax);
+  bool ok = d >= Dlo && d <= Dhi && d <= g.Dmax;
+  if (ok) {
+    uint64_t raw = g.raw(key), v = vol_raw<DIM>(g, d);
+    ok = (raw % v) == 0 && raw < total;
+    uint64_t next = (i + 1 < n) ? g.raw(k[i + 1]) : total;
+    ok = ok && raw + v == next;
+    if (i == 0) ok = ok && raw == 0;
+  }
+  if (!ok) atomicExch(bad, 1);
+}
+
+int read_bad(const int32_t* d_bad, bool* bad, cudaStream_t s, Err* err) {
+  int32_t h = 0;
+  FR_CUDA(err, cudaMemcpyAsync(&h, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  *bad = h != 0;
+  return 0;
+}
+
+}  // namespace
+
+#define DIM_DISPATCH(dim, ...)         \
+  do {                                 \
+    if ((dim) == 2) {                  \
+      constexpr int D_ = 2;            \
+      __VA_ARGS__;                     \
+    } else {                           \
+      constexpr int D_ = 3;            \
+      __VA_ARGS__;                     \
+    }                                  \
+  } while (0)
+
+int tree_encode(int dim, const KG& g, const int32_t* d_boxes, int64_t n, uint64_t* d_keys,
+                cudaStream_t s, Err* err) {
+  if (n <= 0) return 0;
+  Alloc A{nullptr, s, err};
+  Scratch S(&A);
+  int32_t* bad = S.get<int32_t>(1);
+  if (!bad) return set_error(err, FR_ENOMEM, "encode scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  DIM_DISPATCH(dim, (k_encode<D_><<<nblk(n), TB, 0, s>>>(d_boxes, n, d_keys, g, bad)));
+  FR_LAUNCH_CHECK(err);
+  bool b = false;
+  FR_TRY(read_bad(bad, &b, s, err));
+  if (b) return set_error(err, FR_EINVAL, "box with depth/anchor out of range or misaligned");
+  return 0;
+}
+
+int tree_uniform(int dim, const KG& g, int D, uint64_t* d_keys, cudaStream_t s, Err* err) {
+  int64_t count = int64_t(1) << (dim * D);
+  DIM_DISPATCH(dim, (k_uniform<D_><<<nblk(count), TB, 0, s>>>(d_keys, count, g, D)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int tree_linearise(int dim, const KG& g, uint64_t* d_keys, int64_t n, Buf<uint64_t>& out,
+                   int64_t* n_out, Alloc& A, cudaStream_t s, Err* err) {
+  Scratch S(&A);
+  int32_t* cnt = S.get<int32_t>(n);
+  int64_t* offs = S.get<int64_t>(n);
+  int64_t* tot = S.get<int64_t>(1);
+  if (!cnt || !offs || !tot) return set_error(err, FR_ENOMEM, "linearise scratch");
+  if (n > 0) {
+    DIM_DISPATCH(dim, (k_lin_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, n, g, cnt)));
+    FR_LAUNCH_CHECK(err);
+  }
+  FR_TRY(scan_counts(cnt, offs, n, tot, S, s, err));
+  FR_TRY(read_i64(tot, n_out, s, err));
+  FR_TRY(out.ensure(A, size_t(*n_out)));
+  if (n > 0) {
+    k_compact<<<nblk(n), TB, 0, s>>>(d_keys, cnt, offs, n, out.p);
+    FR_LAUNCH_CHECK(err);
+  }
+  return 0;
+}
+
+int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
+              int64_t n, Buf<uint64_t>& out, int64_t* n_out, int64_t* n_ref, int64_t* n_coarse,
+              Alloc& A, cudaStream_t s, Err* err) {
+  Scratch S(&A);
+  int8_t* act = S.get<int8_t>(n);
+  int32_t* cnt = S.get<int32_t>(n);
+  int64_t* offs = S.get<int64_t>(n);
+  int64_t* tot = S.get<int64_t>(1);
+  unsigned long long* st = S.get<unsigned long long>(2);
+  if (!act || !cnt || !offs || !tot || !st) return set_error(err, FR_ENOMEM, "edit scratch");
+  FR_CUDA(err, cudaMemsetAsync(st, 0, 16, s));
+  DIM_DISPATCH(dim, (k_edit_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, d_flags, n, g, Dbase, act, cnt)));
+  FR_LAUNCH_CHECK(err);
+  FR_TRY(scan_counts(cnt, offs, n, tot, S, s, err));
+  FR_TRY(read_i64(tot, n_out, s, err));
+  FR_TRY(out.ensure(A, size_t(*n_out)));
+  DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p, st)));
+  FR_LAUNCH_CHECK(err);
+  unsigned long long h[2] = {0, 0};
+  FR_CUDA(err, cudaMemcpyAsync(h, st, 16, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  if (n_ref) *n_ref = int64_t(h[0]);
+  if (n_coarse) *n_coarse = int64_t(h[1]);
+  return 0;
+}
+
+int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n_io, int* passes,
+                 Alloc& A, cudaStream_t s, Err* err) {
+  const int NO = dim == 2 ? 8 : 26;
+  if (passes) *passes = 0;
+  Buf<uint64_t> gen, tmp, lin, out;
+  int rc = 0;
+  for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
+    int64_t n = *n_io;
+    Scratch S(&A);
+    int32_t* cnt = S.get<int32_t>(n * NO);
+    int64_t* offs = S.get<int64_t>(n * NO);
+    int64_t* tot = S.get<int64_t>(1);
+    if (!cnt || !offs || !tot) {
+      rc = set_error(err, FR_ENOMEM, "balance scratch");
+      break;
+    }
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n * NO), TB, 0, s>>>(keys.p, n, g, D, cnt)));
+    ++launch_counter();
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
+    if ((rc = scan_counts(cnt, offs, n * NO, tot, S, s, err))) break;
+    int64_t G = 0;
+    if ((rc = read_i64(tot, &G, s, err))) break;
+    if (G == 0) continue;
+    if (passes) ++*passes;
+    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G)))) break;
+    DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n * NO), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
+    ++launch_counter();
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_gen") : 0)) break;
+    if ((rc = radix_sort_keys(gen.p, tmp.p, G, dim * g.Dmax + g.mb, S, s, err))) break;
+    int64_t nS = 0;
+    if ((rc = tree_linearise(dim, g, gen.p, G, lin, &nS, A, s, err))) break;
+    int32_t* cnt2 = S.get<int32_t>(n);
+    int64_t* lo = S.get<int64_t>(n);
+    int64_t* offs2 = S.get<int64_t>(n);
+    if (!cnt2 || !lo || !offs2) {
+      rc = set_error(err, FR_ENOMEM, "balance merge scratch");
+      break;
+    }
+    DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, lin.p, nS, g, cnt2, lo)));
+    ++launch_counter();
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_count") : 0)) break;
+    if ((rc = scan_counts(cnt2, offs2, n, tot, S, s, err))) break;
+    int64_t Mn = 0;
+    if ((rc = read_i64(tot, &Mn, s, err))) break;
+    if ((rc = out.ensure(A, size_t(Mn)))) break;
+    k_merge_write<<<nblk(n), TB, 0, s>>>(keys.p, n, lin.p, cnt2, lo, offs2, out.p);
+    ++launch_counter();
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_write") : 0)) break;
+    // out becomes the tree
+    Buf<uint64_t> t = keys;
+    keys = out;
+    out = t;
+    *n_io = Mn;
+  }
+  gen.release(A);
+  tmp.release(A);
+  lin.release(A);
+  out.release(A);
+  return rc;
+}
+
+int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
+             int64_t n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad, cudaStream_t s, Err* err) {
+  if (n_new <= 0) return 0;
+  DIM_DISPATCH(dim, (k_map<D_><<<nblk(n_new), TB, 0, s>>>(d_old, n_old, d_new, n_new, g, d_src, d_tag, d_bad)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+              int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
+              Err* err) {
+  if (n <= 0) return 0;
+  int64_t T = n * 2 * dim;
+  DIM_DISPATCH(dim, (k_conn<D_><<<nblk(T), TB, 0, s>>>(d_keys, n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int tree_validate(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
+                  bool* ok, Alloc& A, cudaStream_t s, Err* err) {
+  Scratch S(&A);
+  int32_t* bad = S.get<int32_t>(1);
+  if (!bad) return set_error(err, FR_ENOMEM, "validate scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  if (n > 0) {
+    DIM_DISPATCH(dim, (k_validate<D_><<<nblk(n), TB, 0, s>>>(d_keys, n, g, Dlo, Dhi, bad)));
+    FR_LAUNCH_CHECK(err);
+  }
+  bool b = true;
+  FR_TRY(read_bad(bad, &b, s, err));
+  *ok = !b && n > 0;
+  return 0;
+}
+
+}  // namespace frg

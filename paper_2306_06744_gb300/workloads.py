@@ -86,14 +86,14 @@ def config(name: str) -> dict:
                         max 7, 500 steps.
     vortex3d_p3_multi : 3D, p=3, periodic [0,80]^3, four seeded tubes (seed 3, beta in [3,6],
                         pairwise separation >= 16), base 5, max 10.
-    The indicator thresholds of the 2D p=3 and 3D cases are chosen so that the leaf counts fall
-    in the stated ranges.
+    The 2D p=3 thresholds (1e-8, 2.5e-9) refine wherever the density varies by more than about the
+    p=3 error level across an element; a single core-1 vortex then gives about 11k leaves.
     """
     if name == "vortex2d_p2_small":
         return _base()
     if name == "vortex2d_p3":
         return _base(p=3, L=40.0, Dbase=5, Dmax=9, vort=vortex_centres(1, 1, 40.0),
-                     th_refine=0.004, th_coarsen=0.001, steps=1000)
+                     th_refine=1e-8, th_coarsen=2.5e-9, steps=1000)
     if name == "vortex3d_p2_tube":
         return _base(dim=3, p=2, L=10.0, Dbase=4, Dmax=7, vort=np.array([[5.0, 5.0, 5.0, 1.0]]),
                      th_refine=0.01, th_coarsen=0.002, steps=500)

@@ -1,0 +1,186 @@
+"""GPU parity of the FR solver against the oracle, through the C ABI.
+
+Tolerances: FP64 residuals within 1e-12 relative L2, the solution after 100 steps within 1e-10
+relative L2, tree outputs bit-exact.  The indicator eta = h max|grad rho| is a difference of O(1)
+densities, so its rounding error is absolute (about 1e-15 times the density scale): eta is
+compared with an absolute tolerance of 1e-12 and flags are compared except where eta lies within
+that tolerance of a threshold.  Adaptation parity tests hand the same flags to both sides.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_06744_gb300 import fr
+from paper_2306_06744_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def _cfg(name, **kw):
+    c = W.config(name)
+    c.update(kw)
+    return c
+
+
+def _random_tree(dim, Dbase, Dmax, seed, psplit=0.35):
+    for k in range(50):
+        boxes = W.random_tree_boxes(dim, Dbase, Dmax, seed=seed + 1000 * k, p_split=psplit)
+        keys = O.balance(dim, Dmax, np.sort(O.morton_encode(dim, Dmax, boxes)))
+        if (O.conn(dim, Dmax, keys)[1] == 2).any():
+            return keys
+    raise AssertionError("no nonconforming tree")
+
+
+def _smooth_state(cfg, keys, seed):
+    """Closed-form vortex (oracle) at the points of a tree, plus a seeded smooth perturbation."""
+    dim, p = cfg["dim"], cfg["p"]
+    N, nv = (p + 1) ** dim, dim + 2
+    o = O.operators(p)
+    boxes = O.morton_decode(dim, cfg["Dmax"], keys)
+    fine = cfg["L"] / 2 ** cfg["Dmax"]
+    idx = np.arange(N)
+    pts = []
+    for b in boxes:
+        h = cfg["L"] / 2 ** b[0]
+        X = np.zeros((N, 3))
+        for a in range(dim):
+            X[:, a] = b[1 + a] * fine + 0.5 * h * (o["x"][(idx // (p + 1) ** a) % (p + 1)] + 1)
+        pts.append(X)
+    q = O.exact(cfg, 0.0, np.concatenate(pts)).reshape(len(keys), N, nv).transpose(0, 2, 1).copy()
+    r = W.random_uniform(q.size, seed).reshape(q.shape) - 0.5
+    q *= 1.0 + 0.01 * r
+    return q
+
+
+def test_init_matches_oracle():
+    cfg = _cfg("vortex2d_p2_small")
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    gi, oi = g.info(), o.info()
+    assert abs(gi["dt"] - oi["dt"]) < 1e-14 * oi["dt"]
+    for a, b in zip(g.conn(), o.conn()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax,seed", [(2, 1, 2, 6, 1), (2, 2, 3, 7, 2), (2, 3, 3, 7, 3),
+                                                   (2, 4, 2, 6, 4), (3, 1, 1, 4, 5), (3, 2, 1, 4, 6),
+                                                   (3, 3, 1, 4, 7), (3, 4, 1, 3, 8)])
+def test_rhs_parity_nonconforming(dim, p, Dbase, Dmax, seed):
+    cfg = _cfg("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube", dim=dim, p=p, Dbase=Dbase,
+               Dmax=Dmax, init_passes=0, indicator=2, dt=1e-3)
+    keys = _random_tree(dim, Dbase, Dmax, seed)
+    u = _smooth_state(cfg, keys, seed)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    g.set_state(keys, u)
+    o.set_state(keys, u)
+    Rg, Ro = g.rhs(), o.rhs()
+    assert rel_l2(Rg, Ro) < 1e-12, rel_l2(Rg, Ro)
+    for a, b in zip(g.conn(), o.conn()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 3), (3, 2)])
+def test_freestream_and_conservation(dim, p):
+    cfg = _cfg("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube", dim=dim, p=p, Dbase=2,
+               Dmax=5 if dim == 2 else 4, init_passes=0, indicator=2, dt=1e-3)
+    keys = _random_tree(dim, cfg["Dbase"], cfg["Dmax"], 77)
+    M, nv, N = len(keys), dim + 2, (p + 1) ** dim
+    q = np.array([1.2, 0.5, -0.3, 0.2, 0.0][:nv])
+    q[-1] = 2.5 + 0.5 * (q[1:1 + dim] ** 2).sum() / q[0]
+    g = fr.Mesh(cfg)
+    g.set_state(keys, np.broadcast_to(q[None, :, None], (M, nv, N)).copy())
+    assert np.abs(g.rhs()).max() < 1e-12
+    u = _smooth_state(cfg, keys, 5)
+    g.set_state(keys, u)
+    n0 = g.norms()["integral"]
+    g.step(5)
+    n1 = g.norms()["integral"]
+    assert np.allclose(n0, n1, rtol=1e-13, atol=1e-13)
+
+
+def test_100_steps_with_adaptation():
+    """Config vortex2d_p2_small: 100 SSP-RK3 steps, adaptation every 10 with shared flags."""
+    cfg = _cfg("vortex2d_p2_small")
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    for cycle in range(10):
+        g.step(10)
+        o.step(10)
+        assert rel_l2(g.state(), o.state()) < 1e-10
+        fg, eg = g.flags()
+        fo, eo = o.flags()
+        tol = 1e-12
+        near = (np.abs(eo - cfg["th_refine"]) < tol) | (np.abs(eo - cfg["th_coarsen"]) < tol)
+        assert np.array_equal(fg[~near], fo[~near])
+        assert np.abs(eg - eo).max() < tol
+        st = g.adapt(fg, stats=True)
+        o.adapt(fg)
+        assert np.array_equal(g.leaves(), o.leaves()), cycle
+        assert rel_l2(g.state(), o.state()) < 1e-10
+        assert st["M_new"] == len(o.leaves())
+    ng, no = g.norms(), o.norms()
+    assert abs(ng["l2_rho"] - no["l2_rho"]) < 1e-8 * no["l2_rho"]
+    assert np.allclose(ng["integral"], no["integral"], rtol=1e-12)
+    assert rel_l2(g.state(), o.state()) < 1e-10
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax", [(2, 3, 3, 7), (3, 2, 2, 5)])
+def test_transfer_parity(dim, p, Dbase, Dmax):
+    cfg = _cfg("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube", dim=dim, p=p, Dbase=Dbase,
+               Dmax=Dmax, init_passes=0, indicator=2, dt=1e-3)
+    keys = _random_tree(dim, Dbase, Dmax, 5)
+    u = _smooth_state(cfg, keys, 9)
+    flags = W.random_flags(len(keys), 17, p_refine=0.2, p_coarsen=0.7)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    g.set_state(keys, u)
+    o.set_state(keys, u)
+    g.adapt(flags)
+    o.adapt(flags)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-13
+
+
+def test_run_is_deterministic():
+    cfg = _cfg("vortex2d_p2_small")
+    a, b = fr.Mesh(cfg), fr.Mesh(cfg)
+    a.run(30)
+    b.run(30)
+    assert np.array_equal(a.leaves(), b.leaves())
+    assert np.array_equal(a.state(), b.state())
+
+
+def test_set_state_rejects_bad_tree():
+    cfg = _cfg("vortex2d_p2_small")
+    g = fr.Mesh(cfg)
+    keys = g.leaves()
+    u = g.state()
+    with pytest.raises(fr.FRError) as e:
+        g.set_state(keys[1:], u[1:])  # incomplete
+    assert e.value.code == fr.FR_EINVAL
+    assert np.array_equal(g.leaves(), keys)  # unchanged
+
+
+def test_init_rejects_bad_config():
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(_cfg("vortex2d_p2_small", p=7))
+    assert e.value.code == fr.FR_EINVAL
+    with pytest.raises(fr.FRError):
+        fr.Mesh(_cfg("vortex3d_p2_tube", Dmax=25))
+
+
+def test_3d_tube_init_and_steps():
+    cfg = _cfg("vortex3d_p2_tube", Dbase=2, Dmax=4)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    g.step(3)
+    o.step(3)
+    assert rel_l2(g.state(), o.state()) < 1e-12
