@@ -184,6 +184,23 @@ int fr_morton_encode(int dim, int Dmax, int64_t n, const int32_t* d_boxes, uint6
                      void* stream);
 /* Ascending LSD radix sort of keys in place over the dim*Dmax+m_b significant bits. */
 int fr_keys_sort(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream);
+
+/* Allocation-free key sort.  The paper has no counterpart; this is a convenience of this library.
+   Same result as fr_keys_sort, but the call allocates no device memory at all: no cudaMalloc,
+   cudaMallocAsync, cudaFree or allocator callback.  It is meant for callers that cannot allocate
+   at the point of the call: code whose device memory is fully reserved up front by another
+   framework or a fixed budget, and loops that must not pay for an allocation or the implicit
+   synchronisation an allocation can cause.
+   Scratch lives in one statically sized device array inside the library (about 2.4 MB, held on
+   every GPU that loads the library until the process exits), so n is limited to
+   FR_NOALLOC_SORT_MAX_KEYS; larger n returns FR_EINVAL without touching the keys.
+   The first call on each device looks up that array's device address (cudaGetSymbolAddress);
+   make that first call before any stream capture.  All calls share the one array and every call
+   writes the scratch words it later reads, so no clearing is needed between calls, but calls
+   whose GPU work overlaps (for example on two streams at once) race on the scratch and must be
+   serialised by the caller.  Synchronises `stream` before returning. */
+#define FR_NOALLOC_SORT_MAX_KEYS (1 << 18)
+int fr_keys_sort_noalloc(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream);
 /* Sort, then linearise (Sec. 3.1): drop duplicates and octants that have a descendant in the set.
    d_out may alias nothing; *n_out receives the count (FR_EOVERFLOW if > cap). */
 int fr_keys_linearise(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,

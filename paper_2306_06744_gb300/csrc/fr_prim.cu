@@ -247,4 +247,110 @@ int radix_sort_keys(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bits, Scra
   return 0;
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the key sort (fr_keys_sort_noalloc).  Its scratch is one file-scope
+// device array, sized for FR_NOALLOC_SORT_MAX_KEYS keys and resident on every device that loads
+// the library until the process exits.  In host code the array's name is only a host-side handle,
+// so its device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NA_MAX = FR_NOALLOC_SORT_MAX_KEYS;
+constexpr int64_t NA_NB = (NA_MAX + RS_TILE - 1) / RS_TILE;            // radix tiles
+constexpr int64_t NA_HIST = 256 * NA_NB;                               // digit counters
+constexpr int64_t NA_SNB = (NA_HIST + SCAN_TILE - 1) / SCAN_TILE;      // scan tiles (<= SCAN_TILE)
+static_assert(NA_SNB <= SCAN_TILE, "two-level scan must cover the histogram");
+constexpr size_t na_align(size_t b) { return (b + 255) / 256 * 256; }
+constexpr size_t NA_OFF_TMP = 0;
+constexpr size_t NA_OFF_HIST = NA_OFF_TMP + na_align(sizeof(uint64_t) * NA_MAX);
+constexpr size_t NA_OFF_OFFS = NA_OFF_HIST + na_align(sizeof(int32_t) * NA_HIST);
+constexpr size_t NA_OFF_SUMS = NA_OFF_OFFS + na_align(sizeof(int64_t) * NA_HIST);
+constexpr size_t NA_OFF_SOFF = NA_OFF_SUMS + na_align(sizeof(int64_t) * NA_SNB);
+constexpr size_t NA_OFF_TOT = NA_OFF_SOFF + na_align(sizeof(int64_t) * NA_SNB);
+constexpr size_t NA_BYTES = NA_OFF_TOT + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_sort_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+unsigned char* g_noalloc_ptr[NA_MAX_DEVICES] = {nullptr};
+
+// device address of the scratch array on the current device (looked up on first use)
+int noalloc_scratch(unsigned char** out, Err* err) {
+  int dev = 0;
+  FR_CUDA(err, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(err, FR_EINVAL, "device index too large");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_sort_scratch);
+    if (ce != cudaSuccess || !p)
+      return set_error(err, FR_ECUDA, std::string("cudaGetSymbolAddress(sort scratch): ") +
+                                          cudaGetErrorString(ce));
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
+}  // namespace
+
+int radix_sort_keys_noalloc(uint64_t* d_keys, int64_t n, int bits, cudaStream_t s, Err* err) {
+  if (n < 0) return set_error(err, FR_EINVAL, "n < 0");
+  if (n > NA_MAX)
+    return set_error(err, FR_EINVAL, "fr_keys_sort_noalloc: n exceeds FR_NOALLOC_SORT_MAX_KEYS");
+  if (n <= 1) return 0;
+  unsigned char* base = nullptr;
+  FR_TRY(noalloc_scratch(&base, err));
+  uint64_t* tmp = reinterpret_cast<uint64_t*>(base + NA_OFF_TMP);
+  int32_t* hist = reinterpret_cast<int32_t*>(base + NA_OFF_HIST);
+  int64_t* offs = reinterpret_cast<int64_t*>(base + NA_OFF_OFFS);
+  int64_t* sums = reinterpret_cast<int64_t*>(base + NA_OFF_SUMS);
+  int64_t* soff = reinterpret_cast<int64_t*>(base + NA_OFF_SOFF);
+  int64_t* tot = reinterpret_cast<int64_t*>(base + NA_OFF_TOT);
+  // every scratch word read below is written earlier in the same call (histograms by k_rs_hist,
+  // offsets by the scan), so nothing has to be cleared between calls
+  int nb = int((n + RS_TILE - 1) / RS_TILE);
+  int64_t nh = int64_t(256) * nb;
+  int64_t snb = (nh + SCAN_TILE - 1) / SCAN_TILE;
+  uint64_t* src = d_keys;
+  uint64_t* dst = tmp;
+  for (int ps = 0; ps < (bits + 7) / 8; ++ps) {
+    int shift = ps * 8;
+    k_rs_hist<<<nb, RS_T, 0, s>>>(src, n, shift, hist, nb);
+    FR_LAUNCH_CHECK(err);
+    if (snb == 1) {
+      k_scan_tile<int32_t><<<1, SCAN_T, 0, s>>>(hist, offs, nh, tot);
+      FR_LAUNCH_CHECK(err);
+    } else {
+      k_scan_tile<int32_t><<<unsigned(snb), SCAN_T, 0, s>>>(hist, offs, nh, sums);
+      FR_LAUNCH_CHECK(err);
+      k_scan_tile<int64_t><<<1, SCAN_T, 0, s>>>(sums, soff, snb, tot);
+      FR_LAUNCH_CHECK(err);
+      k_scan_add<<<unsigned((nh + 255) / 256), 256, 0, s>>>(offs, nh, soff);
+      FR_LAUNCH_CHECK(err);
+    }
+    k_rs_scatter<<<nb, RS_T, 0, s>>>(src, dst, n, shift, offs, nb);
+    FR_LAUNCH_CHECK(err);
+    uint64_t* t2 = src;
+    src = dst;
+    dst = t2;
+  }
+  if (src != d_keys)
+    FR_CUDA(err, cudaMemcpyAsync(d_keys, src, size_t(n) * 8, cudaMemcpyDeviceToDevice, s));
+  return 0;
+}
+
 }  // namespace frg
+
+extern "C" int fr_keys_sort_noalloc(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream) {
+  frg::Err* err = frg::global_err();
+  if ((dim != 2 && dim != 3) || Dmax < 1 || Dmax > 30)
+    return frg::set_error(err, FR_EINVAL, "dim/Dmax out of range");
+  int bits = dim * Dmax + frg::depth_bits(Dmax);
+  if (bits > 63) return frg::set_error(err, FR_EINVAL, "dim*Dmax + depth bits exceeds 63");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FR_TRY(frg::radix_sort_keys_noalloc(d_keys, n, bits, s, err));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  return 0;
+}
+

@@ -73,7 +73,9 @@ EXPORTS = ["fr_mesh_init", "fr_mesh_free", "fr_step", "fr_run", "fr_adapt", "fr_
            "fr_norms", "fr_get_leaves", "fr_get_state", "fr_set_state", "fr_get_conn",
            "fr_set_exact", "fr_set_time", "fr_get_info", "fr_last_error", "fr_morton_encode",
            "fr_keys_sort", "fr_keys_linearise", "fr_tree_balance", "fr_tree_adapt", "fr_tree_map",
-           "fr_tree_conn", "fr_profile_enable", "fr_profile_read", "fr_kernel_launches"]
+           "fr_tree_conn", "fr_profile_enable", "fr_profile_read", "fr_kernel_launches",
+           "fr_keys_sort_noalloc"]
+NOALLOC_SORT_MAX_KEYS = 1 << 18
 
 
 def library_path() -> str:
@@ -112,6 +114,7 @@ def load(build_if_missing: bool = True):
     lib.fr_get_info.argtypes = [vp, C.POINTER(FRInfo)]
     lib.fr_morton_encode.argtypes = [C.c_int, C.c_int, i64, vp, vp, vp]
     lib.fr_keys_sort.argtypes = [C.c_int, C.c_int, vp, i64, vp]
+    lib.fr_keys_sort_noalloc.argtypes = [C.c_int, C.c_int, vp, i64, vp]
     lib.fr_keys_linearise.argtypes = [C.c_int, C.c_int, vp, i64, vp, i64, C.POINTER(i64), vp]
     lib.fr_tree_balance.argtypes = [C.c_int, C.c_int, vp, i64, vp, i64, C.POINTER(i64), vp]
     lib.fr_tree_adapt.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, i64, vp, i64, C.POINTER(i64), vp]
@@ -361,6 +364,14 @@ def keys_sort(dim, Dmax, keys, stream=None):
     k = _dev(np.asarray(keys, dtype=np.uint64).view(np.int64), torch.int64)
     _check(load().fr_keys_sort(dim, Dmax, C.c_void_p(k.data_ptr()), k.numel(), _stream_handle(stream)))
     return _to_np_u64(k)
+
+
+def keys_sort_noalloc_(dim, Dmax, d_keys, stream=None):
+    """Allocation-free sort of a CUDA int64 tensor in place (at most NOALLOC_SORT_MAX_KEYS keys):
+    for callers that cannot allocate device memory during the call.  The tensor is the caller's."""
+    _check(load().fr_keys_sort_noalloc(dim, Dmax, C.c_void_p(d_keys.data_ptr()), d_keys.numel(),
+                                       _stream_handle(stream)))
+    return d_keys
 
 
 def keys_linearise(dim, Dmax, keys, stream=None):
