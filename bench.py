@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -326,6 +327,42 @@ def main():
                "h2d_bytes_per_step": bi // args.e2e_steps, "d2h_bytes_per_step": bo // args.e2e_steps}
         del keys_h
 
+    # the other arithmetic forms of the time-step kernels on the same workload and cycles:
+    # same simulated time, so time_to_solution compares forms at their own vortex L2 error
+    forms = {"f64": {"value": value, "l2_rho": norms["l2_rho"], "time_to_solution_s": t_tot,
+                     "adaptation_pct": 100.0 * t_adapt / (t_step + t_adapt), "M_final": mesh.M,
+                     "stage_kernel_avg_ms": stage_avg_ms}}
+    if not args.no_forms:
+        for prec, name in ((1, "f32_mixed_f64_rk"), (2, "f64x2f32_double_word")):
+            fm = fr.Mesh(dict(cfg, precision=prec), stream=stream)
+            for _ in range(args.warmup):
+                fm.step(ae)
+                fm.adapt()
+            fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+                    torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            fMs = []
+            fm.profile_enable(True)
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                fMs.append(fm.M)
+                a, b, c = fev[k]
+                a.record(stream)
+                fm.step(ae)
+                b.record(stream)
+                fm.adapt()
+                c.record(stream)
+            torch.cuda.synchronize()
+            fp = fm.profile_read()
+            fs = sum(a.elapsed_time(b) for a, b, _ in fev) / 1e3
+            fa = sum(b.elapsed_time(c) for _, b, c in fev) / 1e3
+            fn = fm.norms()
+            forms[name] = {"value": world * sum(ae * m * N * nv for m in fMs) / (fs + fa),
+                           "l2_rho": fn["l2_rho"], "time_to_solution_s": fs + fa,
+                           "adaptation_pct": 100.0 * fa / (fs + fa), "M_final": fm.M,
+                           "stage_kernel_avg_ms": fp["stage_ms"] / max(1, fp["stage_launches"]),
+                           "l2_rel_diff_vs_f64": abs(fn["l2_rho"] - norms["l2_rho"]) / norms["l2_rho"]}
+            fm.close()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = _cpu_baseline(cfg)
@@ -343,6 +380,7 @@ def main():
             "l2_rho": norms["l2_rho"], "t_final": norms["t"], "M_final": mesh.M,
             "M_mean": sum(Ms) / len(Ms), "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "forms": forms,
             "gpu_launches": launches}
     if rank == 0:
         print(json.dumps(line))

@@ -73,7 +73,10 @@ typedef struct {
                               Sec. 5.2 (th_refine, th_coarsen are the radii 5 and 6 of the paper);
                               2: external flags only                                              */
   double th_refine, th_coarsen;
-  int32_t precision;       /* 0: FP64 everywhere (the only form implemented)                      */
+  int32_t precision;       /* arithmetic of the time-step kernels (state, norms and adaptation are
+                              always FP64): 0 FP64; 1 FP32 fluxes, operators, traces and common
+                              fluxes with the Runge-Kutta combination in FP64; 2 double-word
+                              (two-float, ~48-bit significand) on the FP32 pipes                    */
   int32_t init_passes;     /* < 0: Dmax-Dbase passes of {closed-form state, flags, adaptation}    */
 } fr_config;
 

@@ -110,7 +110,7 @@ int check_cfg(const fr_config* c, Err* err) {
   if (c->nvort < 0 || c->nvort > 16 || (c->nvort > 0 && !c->vort))
     return set_error(err, FR_EINVAL, "nvort must be in 0..16 with a vortex array");
   if (c->indicator < 0 || c->indicator > 2) return set_error(err, FR_EINVAL, "bad indicator");
-  if (c->precision != 0) return set_error(err, FR_EINVAL, "only precision 0 (FP64) is implemented");
+  if (c->precision < 0 || c->precision > 2) return set_error(err, FR_EINVAL, "precision must be 0, 1 or 2");
   if (!(c->dt > 0) && !(c->cfl > 0)) return set_error(err, FR_EINVAL, "need dt > 0 or cfl > 0");
   return 0;
 }
@@ -176,7 +176,7 @@ int ensure_state(fr_mesh* m, int64_t M) {
 }
 
 int refresh_traces(fr_mesh* m) {
-  return launch_traces(m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err);
+  return launch_traces(m->cfg.precision, m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err);
 }
 
 FaceArgs face_args(fr_mesh* m) {
@@ -202,7 +202,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
     e2 = m->next_event();
     cudaEventRecord(e0, m->stream);
   }
-  FR_TRY(launch_faces(m->dim, m->p, face_args(m), m->ops, m->stream, &m->err));
+  FR_TRY(launch_faces(m->cfg.precision, m->dim, m->p, face_args(m), m->ops, m->stream, &m->err));
   if (m->prof) {
     cudaEventRecord(e1, m->stream);
     int64_t nsub = int64_t(1) << (m->dim - 1);
@@ -222,7 +222,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.a = a;
   S.b = b;
   S.c = c;
-  FR_TRY(launch_stage(m->dim, m->p, S, m->ops, m->stream, &m->err));
+  FR_TRY(launch_stage(m->cfg.precision, m->dim, m->p, S, m->ops, m->stream, &m->err));
   if (m->prof) {
     cudaEventRecord(e2, m->stream);
     m->recs.push_back({1, e1, e2, m->M * m->N});

@@ -1,0 +1,474 @@
+// fr_kernels.cuh -- the time-step kernels of flux reconstruction (arXiv 2306.06744, Sec. 2.1 and
+// 4.3), templated on the dimension, the number of points per direction n = p+1 and the
+// arithmetic type T (double, float or double-word ff; see fr_arith.cuh).  The state u is FP64 in
+// memory for every T; face traces and common fluxes are stored in T.  Each precision is
+// instantiated in its own translation unit (fr_prec_*.cu).
+#pragma once
+
+#include <type_traits>
+
+#include "fr_arith.cuh"
+#include "fr_internal.cuh"
+#include "fr_solver.cuh"
+
+namespace frg {
+
+// Operator tables in the arithmetic type (passed by value: constant bank)
+template <class T>
+struct OpsT {
+  T Dt[NPMAX][NPMAX];
+  T gL[NPMAX], gR[NPMAX], lm[NPMAX], lp[NPMAX];
+  T I[2][NPMAX][NPMAX];
+  T P[2][NPMAX][NPMAX];
+};
+
+inline double host_conv(double x, double*) { return x; }
+inline float host_conv(double x, float*) { return float(x); }
+inline ff host_conv(double x, ff*) {
+  float h = float(x);
+  float l = float(x - double(h));
+  return ff{h, l};
+}
+
+template <class T>
+OpsT<T> make_ops_t(const DevOps& o) {
+  OpsT<T> r{};
+  T* tag = nullptr;
+  for (int i = 0; i < NPMAX; ++i) {
+    r.gL[i] = host_conv(o.gL[i], tag);
+    r.gR[i] = host_conv(o.gR[i], tag);
+    r.lm[i] = host_conv(o.lm[i], tag);
+    r.lp[i] = host_conv(o.lp[i], tag);
+    for (int j = 0; j < NPMAX; ++j) {
+      r.Dt[i][j] = host_conv(o.Dt[i][j], tag);
+      for (int h = 0; h < 2; ++h) {
+        r.I[h][i][j] = host_conv(o.I[h][i][j], tag);
+        r.P[h][i][j] = host_conv(o.P[h][i][j], tag);
+      }
+    }
+  }
+  return r;
+}
+
+template <int DIM, int NP>
+struct Sz {
+  static constexpr int N = DIM == 2 ? NP * NP : NP * NP * NP;
+  static constexpr int NF = DIM == 2 ? NP : NP * NP;
+  static constexpr int NV = DIM + 2;
+  static constexpr int NFC = 2 * DIM;
+  static constexpr int NSUB = 1 << (DIM - 1);
+  static constexpr int EU = NV * N;         // values per element state
+  static constexpr int EF = NFC * NV * NF;  // values per element face data
+  static constexpr int EPB = (128 / N) > 0 ? (128 / N) : 1;  // elements per 128-thread block
+};
+
+// element point index of position j along `axis` on the line through face point q
+template <int DIM, int NP>
+__device__ __forceinline__ int line_pt(int axis, int q, int j) {
+  if (DIM == 2) return axis == 0 ? j + NP * q : q + NP * j;
+  if (axis == 0) return j + NP * q;
+  if (axis == 1) return (q % NP) + NP * j + NP * NP * (q / NP);
+  return q + NP * NP * j;
+}
+// face point index on the face of `axis` for element point i, and i's position along the axis
+template <int DIM, int NP>
+__device__ __forceinline__ void pt_split(int i, int axis, int* q, int* ia) {
+  int ix = i % NP, iy = (i / NP) % NP, iz = DIM == 3 ? i / (NP * NP) : 0;
+  if (axis == 0) {
+    *ia = ix;
+    *q = DIM == 2 ? iy : iy + NP * iz;
+  } else if (axis == 1) {
+    *ia = iy;
+    *q = DIM == 2 ? ix : ix + NP * iz;
+  } else {
+    *ia = iz;
+    *q = ix + NP * iy;
+  }
+}
+
+// Rusanov common flux along +axis between the minus-side state qL and the plus-side qR, with
+// lambda = max(|u_n| + c) of the two states (Sec. 4.3).
+template <int DIM, class T>
+__device__ __forceinline__ void rusanov_t(const T* qL, const T* qR, int axis, T gam, T gm1, T half,
+                                          T* F) {
+  constexpr int NV = DIM + 2;
+  T rL = rcp_t(qL[0]), rR = rcp_t(qR[0]);
+  T m2L = qL[1] * qL[1], m2R = qR[1] * qR[1];
+#pragma unroll
+  for (int b = 1; b < DIM; ++b) {
+    m2L = fma_t(qL[1 + b], qL[1 + b], m2L);
+    m2R = fma_t(qR[1 + b], qR[1 + b], m2R);
+  }
+  T pL = gm1 * (qL[NV - 1] - half * m2L * rL);
+  T pR = gm1 * (qR[NV - 1] - half * m2R * rR);
+  // normal momenta, selected with unrolled predicates so the state stays in registers
+  T mnL = qL[1], mnR = qR[1];
+#pragma unroll
+  for (int b = 1; b < DIM; ++b)
+    if (b == axis) {
+      mnL = qL[1 + b];
+      mnR = qR[1 + b];
+    }
+  T vL = mnL * rL, vR = mnR * rR;
+  T cL = sqrt_t(gam * pL * rL), cR = sqrt_t(gam * pR * rR);
+  T lam = fmax_t(fabs_t(vL) + cL, fabs_t(vR) + cR);
+  T hl = half * lam;
+  T fL[NV], fR[NV];
+  fL[0] = mnL;
+  fR[0] = mnR;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    T a = qL[1 + b] * vL, c = qR[1 + b] * vR;
+    fL[1 + b] = (b == axis) ? a + pL : a;
+    fR[1 + b] = (b == axis) ? c + pR : c;
+  }
+  fL[NV - 1] = (qL[NV - 1] + pL) * vL;
+  fR[NV - 1] = (qR[NV - 1] + pR) * vR;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
+}
+
+template <class T>
+__device__ __forceinline__ T cst(double x);
+template <>
+__device__ __forceinline__ double cst<double>(double x) {
+  return x;
+}
+template <>
+__device__ __forceinline__ float cst<float>(double x) {
+  return float(x);
+}
+template <>
+__device__ __forceinline__ ff cst<ff>(double x) {
+  return ff_from_double(x);
+}
+
+// traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
+template <int DIM, int NP, class T>
+__global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid_constant__ OpsT<T> ops,
+                           T* __restrict__ tr) {
+  using S = Sz<DIM, NP>;
+  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= M * S::EF) return;
+  int64_t e = idx / S::EF;
+  int r = int(idx % S::EF);
+  int f = r / (S::NV * S::NF), v = (r / S::NF) % S::NV, q = r % S::NF;
+  const T* lf = (f & 1) ? ops.lp : ops.lm;
+  const double* ue = u + (e * S::NV + v) * S::N;
+  T s = zero_t<T>();
+#pragma unroll
+  for (int j = 0; j < NP; ++j) s = fma_t(lf[j], Ar<T>::from_d(ue[line_pt<DIM, NP>(f >> 1, q, j)]), s);
+  tr[idx] = s;
+}
+
+// interface kernel: blocks [0, nb_conf) do conforming faces (one thread per face point), the
+// others do hanging faces (one block slice per coarse face: Rusanov on every mortar piece, then
+// the coarse side's L2 back-projection, owner-computes, Sec. 4.3)
+template <int DIM, int NP, class T>
+__global__ void __launch_bounds__(128) k_faces_t(FaceArgs A, const __grid_constant__ OpsT<T> ops) {
+  using S = Sz<DIM, NP>;
+  constexpr int NV = S::NV, NF = S::NF, NFC = S::NFC, NSUB = S::NSUB;
+  constexpr int PER = NSUB * NF;
+  constexpr int FPB = (128 / PER) > 0 ? 128 / PER : 1;
+  __shared__ T sF[FPB][NSUB][NV][NF];
+  const T* trace = static_cast<const T*>(A.trace);
+  T* fcomm = static_cast<T*>(A.fcomm);
+  const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
+  const int tid = threadIdx.x;
+  if (int64_t(blockIdx.x) < A.nb_conf) {
+    int64_t idx = int64_t(blockIdx.x) * 128 + tid;
+    int64_t face = idx / NF;
+    int q = int(idx % NF);
+    if (face >= A.n_conf) return;
+    int32_t code = A.conf[face];
+    int64_t e = code >> 2;
+    int axis = code & 3;
+    int64_t nb = A.nbr[e * NFC + 2 * axis + 1];
+    T qL[NV], qR[NV], F[NV];
+    const T* tL = trace + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
+    const T* tR = trace + ((nb * NFC + 2 * axis) * NV) * NF + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      qL[v] = tL[v * NF];
+      qR[v] = tR[v * NF];
+    }
+    rusanov_t<DIM, T>(qL, qR, axis, gam, gm1, half, F);
+    T* fL = fcomm + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
+    T* fR = fcomm + ((nb * NFC + 2 * axis) * NV) * NF + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fL[v * NF] = F[v];
+      fR[v * NF] = F[v];
+    }
+    return;
+  }
+  const int64_t hb = int64_t(blockIdx.x) - A.nb_conf;
+  const int lf = tid / PER, r = tid % PER, s = r / NF, q = r % NF;
+  const int64_t hf = hb * FPB + lf;
+  const bool act = lf < FPB && hf < A.n_hang;
+  int64_t ec = 0;
+  int fc = 0;
+  if (act) {
+    int32_t code = A.hang[hf];
+    ec = code >> 3;
+    fc = code & 7;
+    int axis = fc >> 1, sidec = fc & 1;
+    int64_t ek = A.contrib[hf * 4 + s];
+    int fk = fc ^ 1;
+    const T* tc = trace + ((ec * NFC + fc) * NV) * NF;
+    T uc[NV], uf[NV], F[NV];
+    const int q0 = q % NP, h0 = s & 1;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T acc = zero_t<T>();
+      if (DIM == 2) {
+#pragma unroll
+        for (int j0 = 0; j0 < NP; ++j0) acc = fma_t(ops.I[h0][q0][j0], tc[v * NF + j0], acc);
+      } else {
+        const int q1 = q / NP, h1 = s >> 1;
+#pragma unroll
+        for (int j1 = 0; j1 < NP; ++j1) {
+          T a1 = zero_t<T>();
+#pragma unroll
+          for (int j0 = 0; j0 < NP; ++j0) a1 = fma_t(ops.I[h0][q0][j0], tc[v * NF + j0 + NP * j1], a1);
+          acc = fma_t(ops.I[h1][q1][j1], a1, acc);
+        }
+      }
+      uc[v] = acc;
+      uf[v] = trace[((ek * NFC + fk) * NV + v) * NF + q];
+    }
+    if (sidec)
+      rusanov_t<DIM, T>(uc, uf, axis, gam, gm1, half, F);
+    else
+      rusanov_t<DIM, T>(uf, uc, axis, gam, gm1, half, F);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fcomm[((ek * NFC + fk) * NV + v) * NF + q] = F[v];
+      sF[lf][s][v][q] = F[v];
+    }
+  }
+  __syncthreads();
+  if (act && s == 0) {
+    const int q0 = q % NP;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      T acc = zero_t<T>();
+#pragma unroll
+      for (int sp = 0; sp < NSUB; ++sp) {
+        const int h0 = sp & 1;
+        if (DIM == 2) {
+#pragma unroll
+          for (int i0 = 0; i0 < NP; ++i0) acc = fma_t(ops.P[h0][q0][i0], sF[lf][sp][v][i0], acc);
+        } else {
+          const int q1 = q / NP, h1 = sp >> 1;
+#pragma unroll
+          for (int i1 = 0; i1 < NP; ++i1) {
+            T a1 = zero_t<T>();
+#pragma unroll
+            for (int i0 = 0; i0 < NP; ++i0) a1 = fma_t(ops.P[h0][q0][i0], sF[lf][sp][v][i0 + NP * i1], a1);
+            acc = fma_t(ops.P[h1][q1][i1], a1, acc);
+          }
+        }
+      }
+      fcomm[((ec * NFC + fc) * NV + v) * NF + q] = acc;
+    }
+  }
+}
+
+// Runge-Kutta combination type: FP64 for double and float (the mixed form keeps FP64 RK
+// accumulation), double-word for ff.
+template <class T>
+struct RkT {
+  using type = double;
+};
+template <>
+struct RkT<ff> {
+  using type = ff;
+};
+
+// element stage: R = -sum_a (2/h) [ sum_j Dt_ij f_j + gL_i F(-1) + gR_i F(+1) ] along each axis
+// (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt), then
+// out = a*un + b*us + c*R (Eq. rk3), and (optionally) the traces of out.
+template <int DIM, int NP, class T>
+__global__ void __launch_bounds__(128) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
+  using S = Sz<DIM, NP>;
+  using RT = typename RkT<T>::type;
+  constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF;
+  constexpr int EPB = S::EPB;
+  __shared__ T su[EPB * EU];
+  __shared__ T sfl[EPB * DIM * EU];
+  __shared__ T sfc[EPB * EF];
+  __shared__ double sh2[EPB];
+  const T* fcomm = static_cast<const T*>(A.fcomm);
+  T* trace_out = static_cast<T*>(A.trace_out);
+  const int tid = threadIdx.x;
+  const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
+  for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
+  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
+  if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
+  __syncthreads();
+  const int le = tid / N, i = tid % N;
+  const bool act = le < ne;
+  const T gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
+  RT outv[NV];
+  if (act) {
+    const T* q = su + le * EU;
+    T rho = q[i], rinv = rcp_t(rho), E = q[(NV - 1) * N + i];
+    T vel[DIM];
+    T m2 = zero_t<T>();
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      vel[b] = q[(1 + b) * N + i] * rinv;
+      m2 = fma_t(q[(1 + b) * N + i], vel[b], m2);
+    }
+    T p = gm1 * (E - half * m2);
+    T Ep = E + p;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T* fa = sfl + (le * DIM + a) * EU;
+      fa[i] = q[(1 + a) * N + i];
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        T mv = q[(1 + b) * N + i] * vel[a];
+        fa[(1 + b) * N + i] = (a == b) ? mv + p : mv;
+      }
+      fa[(NV - 1) * N + i] = Ep * vel[a];
+    }
+  }
+  __syncthreads();
+  if (act) {
+    T R[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) R[v] = zero_t<T>();
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      int qf, ia;
+      pt_split<DIM, NP>(i, a, &qf, &ia);
+      const T* fa = sfl + (le * DIM + a) * EU;
+      const T* Fm = sfc + le * EF + (2 * a) * NV * NF + qf;
+      const T* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T d = fma_t(ops.gL[ia], Fm[v * NF], ops.gR[ia] * Fp[v * NF]);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) d = fma_t(ops.Dt[ia][j], fa[v * N + line_pt<DIM, NP>(a, qf, j)], d);
+        R[v] = R[v] + d;
+      }
+    }
+    const double s2 = -sh2[le];
+    const int64_t base = (e0 + le) * EU + i;
+    if constexpr (!std::is_same<T, ff>::value) {
+      // FP64 combination (native FP64 and the mixed FP32 form)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double o = A.b * A.us[base + v * N] + A.c * (s2 * Ar<T>::to_d(R[v]));
+        if (A.a != 0.0) o += A.a * A.un[base + v * N];
+        outv[v] = o;
+      }
+    } else {
+      // double-word combination
+      const ff bb = ff_from_double(A.b), cc = ff_from_double(A.c * s2), aa = ff_from_double(A.a);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        ff o = fma_t(bb, su[le * EU + v * N + i], cc * R[v]);
+        if (A.a != 0.0) o = fma_t(aa, ff_from_double(A.un[base + v * N]), o);
+        outv[v] = o;
+      }
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      if constexpr (std::is_same<T, ff>::value)
+        su[le * EU + v * N + i] = outv[v];
+      else
+        su[le * EU + v * N + i] = Ar<T>::from_d(outv[v]);
+      A.out[(e0 + le) * EU + v * N + i] = Ar<RT>::to_d(outv[v]);
+    }
+  }
+  __syncthreads();
+  if (trace_out) {
+    for (int k = tid; k < ne * EF; k += blockDim.x) {
+      int le2 = k / EF, r = k % EF;
+      int f = r / (NV * NF), v = (r / NF) % NV, qq = r % NF;
+      const T* lf = (f & 1) ? ops.lp : ops.lm;
+      const T* ue = su + le2 * EU + v * N;
+      T s = zero_t<T>();
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[line_pt<DIM, NP>(f >> 1, qq, j)], s);
+      trace_out[e0 * EF + k] = s;
+    }
+  }
+}
+
+// ---- per-precision launch bodies (instantiated in fr_prec_*.cu) ----
+#define FR_NP_DISPATCH(dim, p, ...)                                  \
+  do {                                                               \
+    int np_ = (p) + 1;                                               \
+    if ((dim) == 2) {                                                \
+      constexpr int DD = 2;                                          \
+      if (np_ == 2) { constexpr int NN = 2; __VA_ARGS__; }           \
+      else if (np_ == 3) { constexpr int NN = 3; __VA_ARGS__; }      \
+      else if (np_ == 4) { constexpr int NN = 4; __VA_ARGS__; }      \
+      else if (np_ == 5) { constexpr int NN = 5; __VA_ARGS__; }      \
+      else return set_error(err, FR_EINVAL, "p out of range");     \
+    } else if ((dim) == 3) {                                         \
+      constexpr int DD = 3;                                          \
+      if (np_ == 2) { constexpr int NN = 2; __VA_ARGS__; }           \
+      else if (np_ == 3) { constexpr int NN = 3; __VA_ARGS__; }      \
+      else if (np_ == 4) { constexpr int NN = 4; __VA_ARGS__; }      \
+      else if (np_ == 5) { constexpr int NN = 5; __VA_ARGS__; }      \
+      else return set_error(err, FR_EINVAL, "p out of range");     \
+    } else {                                                         \
+      return set_error(err, FR_EINVAL, "dim out of range");        \
+    }                                                                \
+  } while (0)
+
+inline int ipow_k(int b, int e) {
+  int r = 1;
+  while (e-- > 0) r *= b;
+  return r;
+}
+
+template <class T>
+int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps& o, void* tr,
+                       cudaStream_t s, Err* err) {
+  if (M <= 0) return 0;
+  OpsT<T> ops = make_ops_t<T>(o);
+  int64_t Tn = M * 2 * dim * (dim + 2) * ipow_k(p + 1, dim - 1);
+  unsigned nb = unsigned((Tn + 127) / 128);
+  FR_NP_DISPATCH(dim, p, (k_traces_t<DD, NN, T><<<nb, 128, 0, s>>>(u, M, ops, static_cast<T*>(tr))));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+template <class T>
+int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t s, Err* err) {
+  int NF = ipow_k(p + 1, dim - 1), PER = (1 << (dim - 1)) * NF;
+  int FPB = 128 / PER > 0 ? 128 / PER : 1;
+  A.nb_conf = (A.n_conf * NF + 127) / 128;
+  int64_t nb_hang = (A.n_hang + FPB - 1) / FPB;
+  int64_t nb = A.nb_conf + nb_hang;
+  if (nb == 0) return 0;
+  OpsT<T> ops = make_ops_t<T>(o);
+  FR_NP_DISPATCH(dim, p, (k_faces_t<DD, NN, T><<<unsigned(nb), 128, 0, s>>>(A, ops)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+template <class T>
+int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaStream_t s, Err* err) {
+  if (A.M <= 0) return 0;
+  OpsT<T> ops = make_ops_t<T>(o);
+  FR_NP_DISPATCH(dim, p, ({
+                   using SS = Sz<DD, NN>;
+                   unsigned nb = unsigned((A.M + SS::EPB - 1) / SS::EPB);
+                   k_stage_t<DD, NN, T><<<nb, 128, 0, s>>>(A, ops);
+                 }));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+}  // namespace frg

@@ -8,6 +8,7 @@
 #include <cmath>
 
 #include "fr_internal.cuh"
+#include "fr_kernels.cuh"
 #include "fr_solver.cuh"
 
 namespace frg {
@@ -130,68 +131,9 @@ int build_ops(int p, DevOps* o) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Device helpers
+// Device helpers and the remaining (FP64) kernels
 // ---------------------------------------------------------------------------------------------
 namespace {
-
-template <int DIM, int NP>
-struct Sz {
-  static constexpr int N = DIM == 2 ? NP * NP : NP * NP * NP;
-  static constexpr int NF = DIM == 2 ? NP : NP * NP;
-  static constexpr int NV = DIM + 2;
-  static constexpr int NFC = 2 * DIM;
-  static constexpr int NSUB = 1 << (DIM - 1);
-  static constexpr int EU = NV * N;        // doubles per element state
-  static constexpr int EF = NFC * NV * NF; // doubles per element face data
-  static constexpr int EPB = (128 / N) > 0 ? (128 / N) : 1;  // elements per 128-thread block
-};
-
-// element point index of position j along `axis` on the line through face point q
-template <int DIM, int NP>
-__device__ __forceinline__ int line_pt(int axis, int q, int j) {
-  if (DIM == 2) return axis == 0 ? j + NP * q : q + NP * j;
-  if (axis == 0) return j + NP * q;
-  if (axis == 1) return (q % NP) + NP * j + NP * NP * (q / NP);
-  return q + NP * NP * j;
-}
-// face point index on the face of `axis` for element point i, and i's position along the axis
-template <int DIM, int NP>
-__device__ __forceinline__ void pt_split(int i, int axis, int* q, int* ia) {
-  int ix = i % NP, iy = (i / NP) % NP, iz = DIM == 3 ? i / (NP * NP) : 0;
-  if (axis == 0) { *ia = ix; *q = DIM == 2 ? iy : iy + NP * iz; }
-  else if (axis == 1) { *ia = iy; *q = DIM == 2 ? ix : ix + NP * iz; }
-  else { *ia = iz; *q = ix + NP * iy; }
-}
-
-template <int DIM>
-__device__ __forceinline__ void rusanov(const double* qL, const double* qR, int axis, double gam,
-                                        double* F) {
-  constexpr int NV = DIM + 2;
-  double rL = 1.0 / qL[0], rR = 1.0 / qR[0];
-  double m2L = 0.0, m2R = 0.0;
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) {
-    m2L += qL[1 + b] * qL[1 + b];
-    m2R += qR[1 + b] * qR[1 + b];
-  }
-  double pL = (gam - 1.0) * (qL[NV - 1] - 0.5 * m2L * rL);
-  double pR = (gam - 1.0) * (qR[NV - 1] - 0.5 * m2R * rR);
-  double vL = qL[1 + axis] * rL, vR = qR[1 + axis] * rR;
-  double cL = sqrt(gam * pL * rL), cR = sqrt(gam * pR * rR);
-  double lam = fmax(fabs(vL) + cL, fabs(vR) + cR);
-  double fL[NV], fR[NV];
-  fL[0] = qL[1 + axis];
-  fR[0] = qR[1 + axis];
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) {
-    fL[1 + b] = qL[1 + b] * vL + (b == axis ? pL : 0.0);
-    fR[1 + b] = qR[1 + b] * vR + (b == axis ? pR : 0.0);
-  }
-  fL[NV - 1] = (qL[NV - 1] + pL) * vL;
-  fR[NV - 1] = (qR[NV - 1] + pR) * vR;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) F[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (qR[v] - qL[v]);
-}
 
 // closed-form advected isentropic vortex (Sec. 5.2) at physical point X
 __device__ void vortex_state(const DevProblem& P, int dim, double t, const double* X, double* q) {
@@ -258,225 +200,6 @@ __global__ void k_exact(const uint64_t* __restrict__ keys, int64_t M, KG g, doub
 }
 
 // traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
-template <int DIM, int NP>
-__global__ void k_traces(const double* __restrict__ u, int64_t M, const __grid_constant__ DevOps ops,
-                         double* __restrict__ tr) {
-  using S = Sz<DIM, NP>;
-  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= M * S::EF) return;
-  int64_t e = idx / S::EF;
-  int r = int(idx % S::EF);
-  int f = r / (S::NV * S::NF), v = (r / S::NF) % S::NV, q = r % S::NF;
-  const double* lf = (f & 1) ? ops.lp : ops.lm;
-  const double* ue = u + (e * S::NV + v) * S::N;
-  double s = 0.0;
-#pragma unroll
-  for (int j = 0; j < NP; ++j) s += lf[j] * ue[line_pt<DIM, NP>(f >> 1, q, j)];
-  tr[idx] = s;
-}
-
-// interface kernel: blocks [0, nb_conf) do conforming faces (one thread per face point),
-// the others do hanging faces (one block slice per coarse face: Rusanov on every mortar piece,
-// then the coarse side's L2 back-projection, Sec. 4.3).
-template <int DIM, int NP>
-__global__ void __launch_bounds__(128) k_faces(FaceArgs A, const __grid_constant__ DevOps ops) {
-  using S = Sz<DIM, NP>;
-  constexpr int NV = S::NV, NF = S::NF, NFC = S::NFC, NSUB = S::NSUB;
-  constexpr int PER = NSUB * NF;
-  constexpr int FPB = (128 / PER) > 0 ? 128 / PER : 1;
-  __shared__ double sF[FPB][NSUB][NV][NF];
-  const int tid = threadIdx.x;
-  if (int64_t(blockIdx.x) < A.nb_conf) {
-    int64_t idx = int64_t(blockIdx.x) * 128 + tid;
-    int64_t face = idx / NF;
-    int q = int(idx % NF);
-    if (face >= A.n_conf) return;
-    int32_t code = A.conf[face];
-    int64_t e = code >> 2;
-    int axis = code & 3;
-    int64_t nb = A.nbr[e * NFC + 2 * axis + 1];
-    double qL[NV], qR[NV], F[NV];
-    const double* tL = A.trace + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
-    const double* tR = A.trace + ((nb * NFC + 2 * axis) * NV) * NF + q;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      qL[v] = tL[v * NF];
-      qR[v] = tR[v * NF];
-    }
-    rusanov<DIM>(qL, qR, axis, A.gamma, F);
-    double* fL = A.fcomm + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
-    double* fR = A.fcomm + ((nb * NFC + 2 * axis) * NV) * NF + q;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      fL[v * NF] = F[v];
-      fR[v * NF] = F[v];
-    }
-    return;
-  }
-  const int64_t hb = int64_t(blockIdx.x) - A.nb_conf;
-  const int lf = tid / PER, r = tid % PER, s = r / NF, q = r % NF;
-  const int64_t hf = hb * FPB + lf;
-  const bool act = lf < FPB && hf < A.n_hang;
-  int64_t ec = 0;
-  int fc = 0;
-  if (act) {
-    int32_t code = A.hang[hf];
-    ec = code >> 3;
-    fc = code & 7;
-    int axis = fc >> 1, sidec = fc & 1;
-    int64_t ek = A.contrib[hf * 4 + s];
-    int fk = fc ^ 1;
-    const double* tc = A.trace + ((ec * NFC + fc) * NV) * NF;
-    double uc[NV], uf[NV], F[NV];
-    const int q0 = q % NP, h0 = s & 1;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
-      if (DIM == 2) {
-#pragma unroll
-        for (int j0 = 0; j0 < NP; ++j0) acc += ops.I[h0][q0][j0] * tc[v * NF + j0];
-      } else {
-        const int q1 = q / NP, h1 = s >> 1;
-#pragma unroll
-        for (int j1 = 0; j1 < NP; ++j1) {
-          double a1 = 0.0;
-#pragma unroll
-          for (int j0 = 0; j0 < NP; ++j0) a1 += ops.I[h0][q0][j0] * tc[v * NF + j0 + NP * j1];
-          acc += ops.I[h1][q1][j1] * a1;
-        }
-      }
-      uc[v] = acc;
-      uf[v] = A.trace[((ek * NFC + fk) * NV + v) * NF + q];
-    }
-    if (sidec)
-      rusanov<DIM>(uc, uf, axis, A.gamma, F);
-    else
-      rusanov<DIM>(uf, uc, axis, A.gamma, F);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      A.fcomm[((ek * NFC + fk) * NV + v) * NF + q] = F[v];
-      sF[lf][s][v][q] = F[v];
-    }
-  }
-  __syncthreads();
-  if (act && s == 0) {
-    const int q0 = q % NP;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
-#pragma unroll
-      for (int sp = 0; sp < NSUB; ++sp) {
-        const int h0 = sp & 1;
-        if (DIM == 2) {
-#pragma unroll
-          for (int i0 = 0; i0 < NP; ++i0) acc += ops.P[h0][q0][i0] * sF[lf][sp][v][i0];
-        } else {
-          const int q1 = q / NP, h1 = sp >> 1;
-#pragma unroll
-          for (int i1 = 0; i1 < NP; ++i1) {
-            double a1 = 0.0;
-#pragma unroll
-            for (int i0 = 0; i0 < NP; ++i0) a1 += ops.P[h0][q0][i0] * sF[lf][sp][v][i0 + NP * i1];
-            acc += ops.P[h1][q1][i1] * a1;
-          }
-        }
-      }
-      A.fcomm[((ec * NFC + fc) * NV + v) * NF + q] = acc;
-    }
-  }
-}
-
-// element stage: R = -sum_a (2/h) [ sum_j Dt_ij f_j + gL_i F(-1) + gR_i F(+1) ] along each axis
-// (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt), then
-// out = a*un + b*us + c*R, and (optionally) the traces of out.
-template <int DIM, int NP>
-__global__ void __launch_bounds__(128) k_stage(StageArgs A, const __grid_constant__ DevOps ops) {
-  using S = Sz<DIM, NP>;
-  constexpr int N = S::N, NV = S::NV, NF = S::NF, NFC = S::NFC, EU = S::EU, EF = S::EF;
-  constexpr int EPB = S::EPB;
-  __shared__ double su[EPB * EU];
-  __shared__ double sfl[EPB * DIM * EU];
-  __shared__ double sfc[EPB * EF];
-  __shared__ double sh2[EPB];
-  const int tid = threadIdx.x;
-  const int64_t e0 = int64_t(blockIdx.x) * EPB;
-  const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
-  for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = A.us[e0 * EU + k];
-  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = A.fcomm[e0 * EF + k];
-  if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
-  __syncthreads();
-  const int le = tid / N, i = tid % N;
-  const bool act = le < ne;
-  double outv[NV];
-  if (act) {
-    const double* q = su + le * EU;
-    double rho = q[i], rinv = 1.0 / rho, E = q[(NV - 1) * N + i];
-    double vel[DIM], m2 = 0.0;
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) {
-      vel[b] = q[(1 + b) * N + i] * rinv;
-      m2 += q[(1 + b) * N + i] * vel[b];
-    }
-    double p = (A.gamma - 1.0) * (E - 0.5 * m2);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      double* fa = sfl + (le * DIM + a) * EU;
-      fa[i] = q[(1 + a) * N + i];
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) fa[(1 + b) * N + i] = q[(1 + b) * N + i] * vel[a] + (a == b ? p : 0.0);
-      fa[(NV - 1) * N + i] = (E + p) * vel[a];
-    }
-  }
-  __syncthreads();
-  if (act) {
-    double R[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) R[v] = 0.0;
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      int qf, ia;
-      pt_split<DIM, NP>(i, a, &qf, &ia);
-      const double* fa = sfl + (le * DIM + a) * EU;
-      const double* Fm = sfc + le * EF + (2 * a) * NV * NF + qf;
-      const double* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        double d = ops.gL[ia] * Fm[v * NF] + ops.gR[ia] * Fp[v * NF];
-#pragma unroll
-        for (int j = 0; j < NP; ++j) d += ops.Dt[ia][j] * fa[v * N + line_pt<DIM, NP>(a, qf, j)];
-        R[v] += d;
-      }
-    }
-    const double s2 = -sh2[le];
-    const int64_t base = (e0 + le) * EU + i;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double o = A.b * su[le * EU + v * N + i] + A.c * (s2 * R[v]);
-      if (A.a != 0.0) o += A.a * A.un[base + v * N];
-      outv[v] = o;
-    }
-  }
-  __syncthreads();
-  if (act) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) su[le * EU + v * N + i] = outv[v];
-  }
-  __syncthreads();
-  for (int k = tid; k < ne * EU; k += blockDim.x) A.out[e0 * EU + k] = su[k];
-  if (A.trace_out) {
-    for (int k = tid; k < ne * EF; k += blockDim.x) {
-      int le2 = k / EF, r = k % EF;
-      int f = r / (NV * NF), v = (r / NF) % NV, qq = r % NF;
-      const double* lf = (f & 1) ? ops.lp : ops.lm;
-      const double* ue = su + le2 * EU + v * N;
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) s += lf[j] * ue[line_pt<DIM, NP>(f >> 1, qq, j)];
-      A.trace_out[e0 * EF + k] = s;
-    }
-  }
-}
-
 // Adaptation indicator, one thread per element.  Mode 0 (density gradient, a choice of this
 // library): eta = h max_i |grad rho(x_i)| with the uncorrected local derivative (2/h) D rho, so
 // eta = 2 max_i |D_xi rho|.  Mode 1 (analytic centre, Sec. 5.2): compare the numbers of points
@@ -735,35 +458,24 @@ int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, d
   return 0;
 }
 
-int launch_traces(int dim, int p, const double* u, int64_t M, const DevOps& ops, double* tr,
+int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
                   cudaStream_t s, Err* err) {
-  if (M <= 0) return 0;
-  int64_t T = M * 2 * dim * (dim + 2) * ipow(p + 1, dim - 1);
-  FR_DISPATCH(dim, p, (k_traces<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(u, M, ops, tr)));
-  FR_LAUNCH_CHECK(err);
-  return 0;
+  if (prec == 1) return launch_traces_f32(dim, p, u, M, ops, tr, s, err);
+  if (prec == 2) return launch_traces_ff(dim, p, u, M, ops, tr, s, err);
+  return launch_traces_f64(dim, p, u, M, ops, tr, s, err);
 }
 
-int launch_faces(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {
-  int NF = ipow(p + 1, dim - 1), PER = (1 << (dim - 1)) * NF;
-  int FPB = 128 / PER > 0 ? 128 / PER : 1;
-  A.nb_conf = (A.n_conf * NF + 127) / 128;
-  int64_t nb_hang = (A.n_hang + FPB - 1) / FPB;
-  int64_t nb = A.nb_conf + nb_hang;
-  if (nb == 0) return 0;
-  FR_DISPATCH(dim, p, (k_faces<DD, NN><<<unsigned(nb), 128, 0, s>>>(A, ops)));
-  FR_LAUNCH_CHECK(err);
-  return 0;
+int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {
+  if (prec == 1) return launch_faces_f32(dim, p, A, ops, s, err);
+  if (prec == 2) return launch_faces_ff(dim, p, A, ops, s, err);
+  return launch_faces_f64(dim, p, A, ops, s, err);
 }
 
-int launch_stage(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, Err* err) {
-  if (A.M <= 0) return 0;
-  FR_DISPATCH(dim, p, ({
-                using SS = Sz<DD, NN>;
-                k_stage<DD, NN><<<nb_of(A.M, SS::EPB), 128, 0, s>>>(A, ops);
-              }));
-  FR_LAUNCH_CHECK(err);
-  return 0;
+int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s,
+                 Err* err) {
+  if (prec == 1) return launch_stage_f32(dim, p, A, ops, s, err);
+  if (prec == 2) return launch_stage_ff(dim, p, A, ops, s, err);
+  return launch_stage_f64(dim, p, A, ops, s, err);
 }
 
 int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double t,

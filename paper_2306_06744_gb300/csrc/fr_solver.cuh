@@ -5,8 +5,8 @@
 namespace frg {
 
 struct FaceArgs {
-  const double* trace;    // [M][2dim][nv][Nf] traces of the current stage state
-  double* fcomm;          // [M][2dim][nv][Nf] common flux along +axis
+  const void* trace;      // [M][2dim][nv][Nf] traces of the current stage state (arithmetic type)
+  void* fcomm;            // [M][2dim][nv][Nf] common flux along +axis (arithmetic type)
   const int32_t* nbr;     // [M][2dim]
   const int32_t* conf;    // conforming faces: (minus element << 2) | axis
   const int32_t* hang;    // hanging faces: (coarse element << 3) | coarse face
@@ -19,9 +19,9 @@ struct StageArgs {
   const uint64_t* keys;
   const double* us;     // stage state
   const double* un;     // state at the start of the step (read only when a != 0)
-  const double* fcomm;
+  const void* fcomm;    // common fluxes in the arithmetic type
   double* out;          // a*un + b*us + c*R (may alias us or un element-wise)
-  double* trace_out;    // traces of out, or null
+  void* trace_out;      // traces of out in the arithmetic type, or null
   int64_t M;
   KG g;
   double L, gamma, a, b, c;
@@ -31,10 +31,23 @@ struct Mesh;  // defined in fr_api.cu
 
 int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
                  const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err);
-int launch_traces(int dim, int p, const double* u, int64_t M, const DevOps& ops, double* tr,
+// prec: 0 FP64, 1 FP32 with FP64 Runge-Kutta combination, 2 double-word (two floats)
+int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
                   cudaStream_t s, Err* err);
-int launch_faces(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
-int launch_stage(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, Err* err);
+int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
+int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s,
+                 Err* err);
+// per-precision instantiations (fr_prec_f64.cu, fr_prec_f32.cu, fr_prec_ff.cu)
+#define FR_DECLARE_PREC(sfx)                                                                    \
+  int launch_traces_##sfx(int dim, int p, const double* u, int64_t M, const DevOps& ops,        \
+                          void* tr, cudaStream_t s, Err* err);                                  \
+  int launch_faces_##sfx(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s,         \
+                         Err* err);                                                             \
+  int launch_stage_##sfx(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, \
+                         Err* err);
+FR_DECLARE_PREC(f64)
+FR_DECLARE_PREC(f32)
+FR_DECLARE_PREC(ff)
 // indicator: mode 0 density gradient, 1 analytic centre; flags int8[M], eta double[M] (nullable)
 int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double t,
                      const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
