@@ -20,6 +20,7 @@ struct fr_mesh {
   cudaStream_t stream = nullptr;
   fr_allocator user{};
   bool has_user = false;
+  BlockCache cache;
   Alloc A;
   double t = 0.0, dt = 0.0;
   int64_t step = 0, M = 0;
@@ -59,8 +60,7 @@ inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); 
 // faces per element: conforming faces owned by their minus side (checked on the plus face of
 // each element), coarse sides of hanging faces
 template <int DIM>
-__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int32_t* __restrict__ cc,
-                             int32_t* __restrict__ ch) {
+__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int64_t* __restrict__ c) {
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M) return;
   int a = 0, b = 0;
@@ -70,18 +70,16 @@ __global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int32_
     a += (f & 1) && t == 0;
     b += t == 2;
   }
-  cc[e] = a;
-  ch[e] = b;
+  c[e] = int64_t(a) | (int64_t(b) << 32);  // conforming count low, hanging count high
 }
 
 template <int DIM>
 __global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
-                             int64_t M, const int64_t* __restrict__ oc, const int64_t* __restrict__ oh,
-                             int32_t* __restrict__ conf, int32_t* __restrict__ hang,
-                             int32_t* __restrict__ hcon) {
+                             int64_t M, const int64_t* __restrict__ off, int32_t* __restrict__ conf,
+                             int32_t* __restrict__ hang, int32_t* __restrict__ hcon) {
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M) return;
-  int64_t a = oc[e], b = oh[e];
+  int64_t a = off[e] & 0xFFFFFFFFll, b = off[e] >> 32;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) {
     int8_t t = ftype[e * 2 * DIM + f];
@@ -115,7 +113,9 @@ int check_cfg(const fr_config* c, Err* err) {
   return 0;
 }
 
-int rebuild_conn(fr_mesh* m) {
+// connectivity and face lists of the current tree; `extra_bad` (device flag, may be null) is read
+// in the same host synchronisation
+int rebuild_conn(fr_mesh* m, const int32_t* extra_bad = nullptr) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
   int64_t M = m->M, S = M * m->nfc;
@@ -124,41 +124,43 @@ int rebuild_conn(fr_mesh* m) {
   FR_TRY(m->slot.ensure(m->A, S));
   FR_TRY(m->contrib.ensure(m->A, S * 4));
   Scratch Sc(&m->A);
-  int32_t* bad = Sc.get<int32_t>(1);
-  int32_t* cc = Sc.get<int32_t>(M);
-  int32_t* ch = Sc.get<int32_t>(M);
-  int64_t* oc = Sc.get<int64_t>(M);
-  int64_t* oh = Sc.get<int64_t>(M);
-  int64_t* tot = Sc.get<int64_t>(2);
-  if (!bad || !cc || !ch || !oc || !oh || !tot) return set_error(err, FR_ENOMEM, "conn scratch");
-  FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
+  int32_t* bad = Sc.get<int32_t>(2);
+  int64_t* cnt = Sc.get<int64_t>(M);
+  int64_t* off = Sc.get<int64_t>(M);
+  int64_t* tot = Sc.get<int64_t>(1);
+  if (!bad || !cnt || !off || !tot) return set_error(err, FR_ENOMEM, "conn scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 8, s));
   FR_CUDA(err, cudaMemsetAsync(m->contrib.p, 0xff, size_t(S) * 16, s));
+  if (extra_bad) FR_CUDA(err, cudaMemcpyAsync(bad + 1, extra_bad, 4, cudaMemcpyDeviceToDevice, s));
   FR_TRY(tree_conn(m->dim, m->g, m->keys.p, M, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
   if (m->dim == 2)
-    k_face_count<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cc, ch);
+    k_face_count<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cnt);
   else
-    k_face_count<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cc, ch);
+    k_face_count<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cnt);
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts(cc, oc, M, tot, Sc, s, err));
-  FR_TRY(scan_counts(ch, oh, M, tot + 1, Sc, s, err));
-  int64_t h[2];
-  int32_t hb = 0;
-  FR_CUDA(err, cudaMemcpyAsync(h, tot, 16, cudaMemcpyDeviceToHost, s));
-  FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
-  FR_CUDA(err, cudaStreamSynchronize(s));
-  if (hb) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
-  m->n_conf = h[0];
-  m->n_hang = h[1];
-  FR_TRY(m->conf.ensure(m->A, m->n_conf));
-  FR_TRY(m->hang.ensure(m->A, m->n_hang));
+  FR_TRY(scan_counts64(cnt, off, M, tot, Sc, s, err));
+  // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
+  // bound so the writes need no further synchronisation
+  FR_TRY(m->conf.ensure(m->A, size_t(M) * m->dim));
+  FR_TRY(m->hang.ensure(m->A, size_t(M) * m->nfc));
   Buf<int32_t> hcon;
-  FR_TRY(hcon.ensure(m->A, m->n_hang * 4));
+  FR_TRY(hcon.ensure(m->A, size_t(M) * m->nfc * 4));
   if (m->dim == 2)
-    k_face_write<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, oc, oh, m->conf.p, m->hang.p, hcon.p);
+    k_face_write<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, off, m->conf.p, m->hang.p, hcon.p);
   else
-    k_face_write<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, oc, oh, m->conf.p, m->hang.p, hcon.p);
+    k_face_write<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, off, m->conf.p, m->hang.p, hcon.p);
   FR_LAUNCH_CHECK(err);
-  // keep the per-hanging-face contributor table in `contrib` (per element-face table is not
+  int64_t h = 0;
+  int32_t hb[2] = {0, 0};
+  FR_CUDA(err, cudaMemcpyAsync(&h, tot, 8, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  if (hb[0]) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
+  if (hb[1])
+    return set_error(err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
+  m->n_conf = h & 0xFFFFFFFFll;
+  m->n_hang = h >> 32;
+  // keep the per-hanging-face contributor table in `contrib` (the per element-face table is not
   // needed after the lists are built)
   Buf<int32_t> old = m->contrib;
   m->contrib = hcon;
@@ -300,6 +302,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<int32_t> src;
   Buf<int8_t> tag;
   Scratch Sc(&m->A);
+  const int32_t* map_bad = nullptr;
   if (transfer) {
     int32_t* bad = Sc.get<int32_t>(1);
     if (!bad) rc = set_error(err, FR_ENOMEM, "adapt scratch");
@@ -310,10 +313,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     T.mark(1);
     if (!rc) rc = nu.ensure(m->A, size_t(M1) * m->EU);
     if (!rc) rc = launch_transfer(m->dim, m->p, m->g, m->keys.p, nk.p, src.p, tag.p, M1, m->ops, m->u.p, nu.p, s, err);
-    int32_t hb = 0;
-    if (!rc && cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
-        cudaStreamSynchronize(s) == cudaSuccess && hb)
-      rc = set_error(err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
+    map_bad = bad;
   } else {
     T.mark(1);
   }
@@ -340,7 +340,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   FR_TRY(m->fcomm.ensure(m->A, size_t(M1) * m->EF));
   FR_TRY(m->flags.ensure(m->A, size_t(M1)));
   if (!transfer) FR_TRY(m->u.ensure(m->A, size_t(M1) * m->EU));
-  FR_TRY(rebuild_conn(m));
+  FR_TRY(rebuild_conn(m, map_bad));
   if (transfer) FR_TRY(refresh_traces(m));
   T.mark(3);
   if (st) {
@@ -393,7 +393,7 @@ int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void*
     m->user = *alloc;
     m->has_user = true;
   }
-  m->A = Alloc{m->has_user ? &m->user : nullptr, m->stream, err};
+  m->A = Alloc{m->has_user ? &m->user : nullptr, m->stream, err, &m->cache};
   int devcount = 0;
   if (cudaGetDeviceCount(&devcount) != cudaSuccess || devcount == 0) {
     cudaGetLastError();
@@ -449,6 +449,11 @@ void free_all(fr_mesh* m) {
   m->norm_part.release(m->A);
   m->norm_out.release(m->A);
   m->dmax.release(m->A);
+  m->A.release_cache();
+  // blocks still handed out (none after a clean release) go back to the allocator as well
+  auto live = m->cache.live;
+  for (auto& b : live) m->A.put(b.first);
+  m->A.release_cache();
 }
 
 int host_copy(Err* err, void* dst, const void* src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) {

@@ -180,12 +180,22 @@ __device__ __forceinline__ int64_t upper_bound_dev(const uint64_t* a, int64_t n,
 // ---------------------------------------------------------------------------------------------
 // Device memory: caller allocator or stream-ordered cudaMallocAsync.
 // ---------------------------------------------------------------------------------------------
+// Blocks released by a mesh are kept for reuse on the same stream (stream order makes the reuse
+// safe) instead of going back to the caller's allocator every time; they are returned at
+// fr_mesh_free.
+struct BlockCache {
+  std::vector<std::pair<void*, size_t>> free_blocks;
+  std::vector<std::pair<void*, size_t>> live;  // block -> size of blocks handed out
+};
+
 struct Alloc {
   const fr_allocator* user = nullptr;
   cudaStream_t stream = nullptr;
   Err* err = nullptr;
+  BlockCache* cache = nullptr;
   void* get(size_t bytes);
   void put(void* p);
+  void release_cache();
 };
 
 template <class T>
@@ -233,6 +243,8 @@ struct Scratch {
 // exclusive scan of int32 counts into int64 offsets; the total goes to *d_total (device)
 int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
                 cudaStream_t s, Err* err);
+int scan_counts64(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                  cudaStream_t s, Err* err);
 // ascending LSD radix sort of n keys over the low `bits` bits; d_tmp holds n keys of scratch
 int radix_sort_keys(uint64_t* d_keys, uint64_t* d_tmp, int64_t n, int bits, Scratch& S,
                     cudaStream_t s, Err* err);

@@ -27,9 +27,8 @@ Err* global_err() {
   return &e;
 }
 
-void* Alloc::get(size_t bytes) {
+static void* raw_get(const fr_allocator* user, cudaStream_t stream, size_t bytes) {
   void* p = nullptr;
-  if (bytes == 0) bytes = 16;
   if (user && user->alloc) {
     p = user->alloc(bytes, (void*)stream, user->ctx);
   } else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
@@ -39,12 +38,53 @@ void* Alloc::get(size_t bytes) {
   return p;
 }
 
-void Alloc::put(void* p) {
-  if (!p) return;
+static void raw_put(const fr_allocator* user, cudaStream_t stream, void* p) {
   if (user && user->free)
     user->free(p, (void*)stream, user->ctx);
   else
     cudaFreeAsync(p, stream);
+}
+
+void* Alloc::get(size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) / 256 * 256;
+  if (cache) {
+    // smallest cached block that fits without wasting more than half of it
+    size_t best = size_t(-1);
+    for (size_t k = 0; k < cache->free_blocks.size(); ++k) {
+      size_t sz = cache->free_blocks[k].second;
+      if (sz >= bytes && sz <= 2 * bytes + 4096 && (best == size_t(-1) || sz < cache->free_blocks[best].second))
+        best = k;
+    }
+    if (best != size_t(-1)) {
+      auto blk = cache->free_blocks[best];
+      cache->free_blocks.erase(cache->free_blocks.begin() + long(best));
+      cache->live.push_back(blk);
+      return blk.first;
+    }
+  }
+  void* p = raw_get(user, stream, bytes);
+  if (p && cache) cache->live.push_back({p, bytes});
+  return p;
+}
+
+void Alloc::put(void* p) {
+  if (!p) return;
+  if (cache) {
+    for (size_t k = 0; k < cache->live.size(); ++k)
+      if (cache->live[k].first == p) {
+        cache->free_blocks.push_back(cache->live[k]);
+        cache->live.erase(cache->live.begin() + long(k));
+        return;
+      }
+  }
+  raw_put(user, stream, p);
+}
+
+void Alloc::release_cache() {
+  if (!cache) return;
+  for (auto& b : cache->free_blocks) raw_put(user, stream, b.first);
+  cache->free_blocks.clear();
 }
 
 int read_i64(const int64_t* d, int64_t* h, cudaStream_t s, Err* err) {
@@ -149,6 +189,11 @@ static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_tota
 int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
                 cudaStream_t s, Err* err) {
   return scan_impl<int32_t>(d_in, d_out, n, d_total, S, s, err);
+}
+
+int scan_counts64(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                  cudaStream_t s, Err* err) {
+  return scan_impl<int64_t>(d_in, d_out, n, d_total, S, s, err);
 }
 
 // ---------------------------------------------------------------------------------------------

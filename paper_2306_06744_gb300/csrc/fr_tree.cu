@@ -171,13 +171,42 @@ __global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t n, KG g, int D
   }
 }
 
+// Sort of a small key set inside one block: bitonic network over a power-of-two padded array in
+// shared memory (padding = all-ones keys, which sort last and are not written back).
+constexpr int SMALL_SORT_MAX = 4096;
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t n) {
+  __shared__ uint64_t sk[SMALL_SORT_MAX];
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < n ? keys[i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          uint64_t a = sk[i], b = sk[l];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            sk[i] = b;
+            sk[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = sk[i];
+}
+
 // replace every leaf by the linearised generated octants inside it (or keep it)
 template <int DIM>
 __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t n,
-                              const uint64_t* __restrict__ S, int64_t nS, KG g,
+                              const uint64_t* __restrict__ S, const int64_t* __restrict__ d_nS, KG g,
                               int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t nS = *d_nS;
   uint64_t key = k[i];
   int64_t lo = lower_bound_dev(S, nS, key);
   int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
@@ -378,22 +407,24 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   int8_t* act = S.get<int8_t>(n);
   int32_t* cnt = S.get<int32_t>(n);
   int64_t* offs = S.get<int64_t>(n);
-  int64_t* tot = S.get<int64_t>(1);
-  unsigned long long* st = S.get<unsigned long long>(2);
-  if (!act || !cnt || !offs || !tot || !st) return set_error(err, FR_ENOMEM, "edit scratch");
-  FR_CUDA(err, cudaMemsetAsync(st, 0, 16, s));
+  int64_t* res = S.get<int64_t>(3);  // [0] refined, [1] coarsened groups, [2] new leaf count
+  if (!act || !cnt || !offs || !res) return set_error(err, FR_ENOMEM, "edit scratch");
+  // the edited tree has at most 2^dim leaves per old leaf: size the output for that bound so
+  // that the count, the scan and the write need a single host synchronisation at the end
+  FR_TRY(out.ensure(A, size_t(n) << dim));
+  FR_CUDA(err, cudaMemsetAsync(res, 0, 16, s));
   DIM_DISPATCH(dim, (k_edit_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, d_flags, n, g, Dbase, act, cnt)));
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts(cnt, offs, n, tot, S, s, err));
-  FR_TRY(read_i64(tot, n_out, s, err));
-  FR_TRY(out.ensure(A, size_t(*n_out)));
-  DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p, st)));
+  FR_TRY(scan_counts(cnt, offs, n, res + 2, S, s, err));
+  DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p,
+                                                               reinterpret_cast<unsigned long long*>(res))));
   FR_LAUNCH_CHECK(err);
-  unsigned long long h[2] = {0, 0};
-  FR_CUDA(err, cudaMemcpyAsync(h, st, 16, cudaMemcpyDeviceToHost, s));
+  int64_t h[3] = {0, 0, 0};
+  FR_CUDA(err, cudaMemcpyAsync(h, res, 24, cudaMemcpyDeviceToHost, s));
   FR_CUDA(err, cudaStreamSynchronize(s));
-  if (n_ref) *n_ref = int64_t(h[0]);
-  if (n_coarse) *n_coarse = int64_t(h[1]);
+  *n_out = h[2];
+  if (n_ref) *n_ref = h[0];
+  if (n_coarse) *n_coarse = h[1];
   return 0;
 }
 
@@ -421,13 +452,32 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n
     if ((rc = read_i64(tot, &G, s, err))) break;
     if (G == 0) continue;
     if (passes) ++*passes;
-    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G)))) break;
+    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G))) ||
+        (rc = lin.ensure(A, size_t(G))))
+      break;
     DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n * NO), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_gen") : 0)) break;
-    if ((rc = radix_sort_keys(gen.p, tmp.p, G, dim * g.Dmax + g.mb, S, s, err))) break;
-    int64_t nS = 0;
-    if ((rc = tree_linearise(dim, g, gen.p, G, lin, &nS, A, s, err))) break;
+    if (G <= SMALL_SORT_MAX) {
+      k_sort_small<<<1, 1024, 0, s>>>(gen.p, G);
+      ++launch_counter();
+      if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_sort_small") : 0)) break;
+    } else if ((rc = radix_sort_keys(gen.p, tmp.p, G, dim * g.Dmax + g.mb, S, s, err))) {
+      break;
+    }
+    // linearise the generated octants (sorted): the count stays on the device
+    int32_t* cl = S.get<int32_t>(G);
+    int64_t* ol = S.get<int64_t>(G);
+    int64_t* nS = S.get<int64_t>(1);
+    if (!cl || !ol || !nS) {
+      rc = set_error(err, FR_ENOMEM, "balance linearise scratch");
+      break;
+    }
+    DIM_DISPATCH(dim, (k_lin_count<D_><<<nblk(G), TB, 0, s>>>(gen.p, G, g, cl)));
+    ++launch_counter();
+    if ((rc = scan_counts(cl, ol, G, nS, S, s, err))) break;
+    k_compact<<<nblk(G), TB, 0, s>>>(gen.p, cl, ol, G, lin.p);
+    ++launch_counter();
     int32_t* cnt2 = S.get<int32_t>(n);
     int64_t* lo = S.get<int64_t>(n);
     int64_t* offs2 = S.get<int64_t>(n);
