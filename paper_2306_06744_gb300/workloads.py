@@ -87,7 +87,9 @@ def config(name: str) -> dict:
     vortex3d_p3_multi : 3D, p=3, periodic [0,80]^3, four seeded tubes (seed 3, beta in [3,6],
                         pairwise separation >= 16), base 5, max 10.
     The 2D p=3 thresholds (1e-8, 2.5e-9) refine wherever the density varies by more than about the
-    p=3 error level across an element; a single core-1 vortex then gives about 11k leaves.
+    p=3 error level across an element; a single core-1 vortex then gives 19k-26k leaves.  The 3D
+    thresholds put the initial meshes in the stated ranges: 177k leaves for the tube (50k-200k)
+    and 2.95M for the four tubes (2M-4M).
     """
     if name == "vortex2d_p2_small":
         return _base()
@@ -96,11 +98,11 @@ def config(name: str) -> dict:
                      th_refine=1e-8, th_coarsen=2.5e-9, steps=1000)
     if name == "vortex3d_p2_tube":
         return _base(dim=3, p=2, L=10.0, Dbase=4, Dmax=7, vort=np.array([[5.0, 5.0, 5.0, 1.0]]),
-                     th_refine=0.01, th_coarsen=0.002, steps=500)
+                     th_refine=0.03, th_coarsen=0.0075, steps=500)
     if name == "vortex3d_p3_multi":
         return _base(dim=3, p=3, L=80.0, Dbase=5, Dmax=10,
                      vort=vortex_centres(3, 4, 80.0, min_sep=16.0, beta_range=(3.0, 6.0)),
-                     th_refine=0.01, th_coarsen=0.002, steps=100)
+                     th_refine=0.05, th_coarsen=0.0125, steps=100)
     raise KeyError(name)
 
 
