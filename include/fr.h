@@ -208,6 +208,15 @@ int fr_keys_sort_noalloc(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* s
    d_out may alias nothing; *n_out receives the count (FR_EOVERFLOW if > cap). */
 int fr_keys_linearise(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,
                       int64_t cap, int64_t* n_out, void* stream);
+/* Tree completion from scattered points (Sec. 3.1, construction algorithm; Sec. 5.1 uses a
+   background at Dmin and encodes the points at Dmax): d_pts double[n][dim] in [0,L)^dim (points
+   outside are clamped to the boundary cells).  Output: the coarsest complete sorted linear tree
+   whose leaves are at depth >= Dmin and which holds the depth-Dmax cell of every point as a leaf.
+   It is not 2:1 balanced (apply fr_tree_balance).  Each gap between consecutive seed cells is
+   covered by the largest aligned octants that fit, written at scanned positions, so no
+   shared-memory overflow or retry exists.  *n_out receives the leaf count (FR_EOVERFLOW if > cap). */
+int fr_tree_complete(int dim, int Dmin, int Dmax, double L, const double* d_pts, int64_t n,
+                     uint64_t* d_out, int64_t cap, int64_t* n_out, void* stream);
 /* 2:1 balance (Sec. 3.2, strong/vertex balance, periodic) of a complete sorted linear tree: the
    coarsest balanced refinement.  Depth passes from Dmax down to 2. */
 int fr_tree_balance(int dim, int Dmax, const uint64_t* d_keys, int64_t n, uint64_t* d_out,

@@ -122,6 +122,22 @@ def balance(dim, Dmax, keys):
     return out[: nout.value].copy()
 
 
+def tree_complete(dim, Dmin, Dmax, L, pts):
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, dim)
+    cap = 1024
+    while True:
+        out = np.zeros(cap, dtype=np.uint64)
+        nout = C.c_int64(0)
+        rc = lib().oracle_tree_complete(dim, Dmin, Dmax, C.c_double(L), _ptr(pts, C.c_double),
+                                        C.c_int64(pts.shape[0]), _ptr(out, C.c_uint64),
+                                        C.c_int64(cap), C.byref(nout))
+        if rc == -3 and nout.value > cap:
+            cap = nout.value
+            continue
+        _check(rc)
+        return out[: nout.value].copy()
+
+
 def adapt_keys(dim, Dbase, Dmax, keys, flags):
     keys = np.ascontiguousarray(keys, dtype=np.uint64)
     flags = np.ascontiguousarray(flags, dtype=np.int8)

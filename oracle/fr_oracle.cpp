@@ -187,6 +187,32 @@ std::vector<uint64_t> linearise(const Geo& g, std::vector<uint64_t> v) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Tree completion from scattered points (Sec. 3.1, construction algorithm; Sec. 5.1: a coarse
+// background at Dmin, points encoded at Dmax).  Definition written out: starting from the root,
+// an octant is split while its depth is below Dmin, or while it contains the finest cell of some
+// point and is above Dmax; every other octant is a leaf.  Point cells: floor(x / L * 2^Dmax),
+// clamped to the grid.
+// ------------------------------------------------------------------------------------------
+void complete_rec(const Geo& g, int Dmin, const std::set<uint64_t>& cells, const Box& o,
+                  std::vector<uint64_t>& out) {
+  bool split = o.depth < Dmin;
+  if (!split && o.depth < g.Dmax) {
+    // does o contain a point cell?  cells are depth-Dmax keys; those inside o lie in [lo, hi]
+    uint64_t k = encode(g, o);
+    uint64_t lo = (k >> g.mb) << g.mb;
+    uint64_t vol = uint64_t(1) << (g.dim * (g.Dmax - o.depth));
+    uint64_t hi = (((k >> g.mb) + vol - 1) << g.mb) | ((uint64_t(1) << g.mb) - 1);
+    auto it = cells.lower_bound(lo);
+    split = it != cells.end() && *it <= hi;
+  }
+  if (!split) {
+    out.push_back(encode(g, o));
+    return;
+  }
+  for (int c = 0; c < (1 << g.dim); ++c) complete_rec(g, Dmin, cells, child_box(g, o, c), out);
+}
+
+// ------------------------------------------------------------------------------------------
 // 2:1 balance (Sec. 3.2).  Reading: strong (vertex) balance with periodic wrap; the result is the
 // unique coarsest balanced refinement.  Definition written out: while some leaf A touches a leaf B
 // more than one level finer, split A.  A coarser leaf A touches B iff A contains the anchor of one
@@ -1026,6 +1052,33 @@ int oracle_linearise(int dim, int Dmax, const uint64_t* keys, int64_t n, uint64_
   if (!geo_ok(dim, Dmax) || n < 0) return fail(ORACLE_EINVAL, "bad geometry");
   Geo g{dim, Dmax, depth_bits(Dmax)};
   std::vector<uint64_t> r = linearise(g, std::vector<uint64_t>(keys, keys + n));
+  *n_out = int64_t(r.size());
+  if (int64_t(r.size()) > cap) return fail(ORACLE_EOVERFLOW, "output capacity too small");
+  std::copy(r.begin(), r.end(), out);
+  return 0;
+}
+
+int oracle_tree_complete(int dim, int Dmin, int Dmax, double L, const double* pts, int64_t n,
+                         uint64_t* out, int64_t cap, int64_t* n_out) {
+  if (!geo_ok(dim, Dmax) || Dmin < 0 || Dmin > Dmax || !(L > 0) || n < 0)
+    return fail(ORACLE_EINVAL, "bad arguments");
+  Geo g{dim, Dmax, depth_bits(Dmax)};
+  int64_t side = int64_t(1) << Dmax;
+  std::set<uint64_t> cells;
+  for (int64_t k = 0; k < n; ++k) {
+    Box b{};
+    b.depth = Dmax;
+    for (int a = 0; a < dim; ++a) {
+      double c = std::floor(pts[k * dim + a] / L * double(side));
+      int64_t ci = c < 0 ? 0 : (c >= double(side) ? side - 1 : int64_t(c));
+      b.x[a] = ci;
+    }
+    cells.insert(encode(g, b));
+  }
+  std::vector<uint64_t> r;
+  Box root{};
+  root.depth = 0;
+  complete_rec(g, Dmin, cells, root, r);
   *n_out = int64_t(r.size());
   if (int64_t(r.size()) > cap) return fail(ORACLE_EOVERFLOW, "output capacity too small");
   std::copy(r.begin(), r.end(), out);

@@ -64,6 +64,10 @@ int oracle_morton_encode(int dim, int Dmax, int64_t n, const int32_t* boxes /*[n
 int oracle_morton_decode(int dim, int Dmax, int64_t n, const uint64_t* keys, int32_t* boxes);
 int oracle_linearise(int dim, int Dmax, const uint64_t* keys, int64_t n, uint64_t* out,
                      int64_t cap, int64_t* n_out);
+/* Tree completion from points pts[n][dim] in [0,L)^dim: coarsest complete tree whose leaves are
+   at depth >= Dmin and which holds every point's depth-Dmax cell as a leaf (Sec. 3.1). */
+int oracle_tree_complete(int dim, int Dmin, int Dmax, double L, const double* pts, int64_t n,
+                         uint64_t* out, int64_t cap, int64_t* n_out);
 int oracle_balance(int dim, int Dmax, const uint64_t* keys, int64_t n, uint64_t* out, int64_t cap,
                    int64_t* n_out);
 int oracle_adapt_keys(int dim, int Dbase, int Dmax, const uint64_t* keys, const int8_t* flags,

@@ -804,6 +804,30 @@ int fr_tree_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys, const in
   return balance_or_adapt(dim, Dbase, Dmax, d_keys, d_flags, n, d_out, cap, n_out, stream);
 }
 
+int fr_tree_complete(int dim, int Dmin, int Dmax, double L, const double* d_pts, int64_t n,
+                     uint64_t* d_out, int64_t cap, int64_t* n_out, void* stream) {
+  int rc;
+  KG g = geo_or_err(dim, Dmax, &rc);
+  if (rc) return rc;
+  if (n < 0 || !n_out || Dmin < 0 || Dmin > Dmax || !(L > 0))
+    return set_error(global_err(), FR_EINVAL, "bad arguments");
+  if (n > (int64_t(1) << 30)) return set_error(global_err(), FR_EINVAL, "too many points");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Err* err = global_err();
+  Alloc A{nullptr, s, err};
+  Buf<uint64_t> out;
+  int64_t m = 0;
+  rc = tree_complete(dim, g, Dmin, L, d_pts, n, out, &m, A, s, err);
+  *n_out = m;
+  if (!rc && m > cap) rc = set_error(err, FR_EOVERFLOW, "output capacity too small");
+  if (!rc && m)
+    rc = cudaMemcpyAsync(d_out, out.p, size_t(m) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess
+             ? 0 : set_error(err, FR_ECUDA, "copy");
+  out.release(A);
+  if (!rc) FR_CUDA(err, cudaStreamSynchronize(s));
+  return rc;
+}
+
 int fr_tree_map(int dim, int Dmax, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
                 int64_t n_new, int32_t* d_src, int8_t* d_tag, void* stream) {
   int rc;

@@ -261,6 +261,8 @@ struct TreeOut {
 int tree_encode(int dim, const KG& g, const int32_t* d_boxes, int64_t n, uint64_t* d_keys,
                 cudaStream_t s, Err* err);
 int tree_uniform(int dim, const KG& g, int D, uint64_t* d_keys, cudaStream_t s, Err* err);
+int tree_complete(int dim, const KG& g, int Dmin, double L, const double* d_pts, int64_t n,
+                  Buf<uint64_t>& out, int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
 int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf<uint64_t>& out,
                    int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,

@@ -335,6 +335,81 @@ __global__ void k_validate(const uint64_t* __restrict__ k, int64_t n, KG g, int 
   if (!ok) atomicExch(bad, 1);
 }
 
+// Tree completion (Sec. 3.1): the finest cell of each point becomes a seed octant; between two
+// consecutive seeds (and before the first / after the last) the Morton interval of finest cells
+// is covered greedily by the largest aligned octants that fit, never coarser than Dmin.  This is
+// the coarsest complete tree holding the seeds as leaves, and it comes out already sorted.
+template <int DIM>
+__global__ void k_pts_encode(const double* __restrict__ pts, int64_t n, double L, KG g,
+                             uint64_t* __restrict__ keys) {
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double side = double(1ull << g.Dmax);
+  uint32_t x[3] = {0, 0, 0};
+  for (int a = 0; a < DIM; ++a) {
+    double c = floor(pts[i * DIM + a] / L * side);
+    x[a] = c < 0.0 ? 0u : (c >= side ? uint32_t(side) - 1u : uint32_t(c));
+  }
+  keys[i] = cell_key<DIM>(g, x);
+}
+
+// greedy decomposition of the raw-ID interval [lo, hi]; emits (raw, depth) when out != null
+template <int DIM>
+__device__ __forceinline__ int64_t gap_blocks(uint64_t lo, uint64_t hi_excl, const KG& g, int Dmin,
+                                              uint64_t* out) {
+  int64_t cnt = 0;
+  const int kmax = g.Dmax - Dmin;
+  while (lo < hi_excl) {
+    int k = 0;
+    while (k < kmax) {
+      uint64_t span = 1ull << (DIM * (k + 1));
+      if ((lo & (span - 1)) != 0 || lo + span > hi_excl) break;
+      ++k;
+    }
+    if (out) out[cnt] = g.make(lo, g.Dmax - k);
+    ++cnt;
+    lo += 1ull << (DIM * k);
+  }
+  return cnt;
+}
+
+template <int DIM>
+__device__ __forceinline__ void gap_bounds(const uint64_t* S, int64_t nS, int64_t t, const KG& g,
+                                           uint64_t* lo, uint64_t* hi_excl) {
+  *lo = t == 0 ? 0ull : g.raw(S[t - 1]) + vol_raw<DIM>(g, g.depth(S[t - 1]));
+  *hi_excl = t == nS ? (1ull << (DIM * g.Dmax)) : g.raw(S[t]);
+}
+
+template <int DIM>
+__global__ void k_gap_count(const uint64_t* __restrict__ S, const int64_t* __restrict__ d_nS,
+                            int64_t ncap, KG g, int Dmin, int32_t* __restrict__ cnt) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t > ncap) return;
+  const int64_t nS = *d_nS;
+  if (t > nS) {
+    cnt[t] = 0;
+    return;
+  }
+  uint64_t lo, hi;
+  gap_bounds<DIM>(S, nS, t, g, &lo, &hi);
+  cnt[t] = int32_t(gap_blocks<DIM>(lo, hi, g, Dmin, nullptr) + (t < nS ? 1 : 0));
+}
+
+template <int DIM>
+__global__ void k_gap_write(const uint64_t* __restrict__ S, const int64_t* __restrict__ d_nS,
+                            int64_t ncap, KG g, int Dmin, const int64_t* __restrict__ offs,
+                            uint64_t* __restrict__ out) {
+  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t > ncap) return;
+  const int64_t nS = *d_nS;
+  if (t > nS) return;
+  uint64_t lo, hi;
+  gap_bounds<DIM>(S, nS, t, g, &lo, &hi);
+  int64_t o = offs[t];
+  int64_t c = gap_blocks<DIM>(lo, hi, g, Dmin, out + o);
+  if (t < nS) out[o + c] = S[t];
+}
+
 int read_bad(const int32_t* d_bad, bool* bad, cudaStream_t s, Err* err) {
   int32_t h = 0;
   FR_CUDA(err, cudaMemcpyAsync(&h, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -369,6 +444,43 @@ int tree_encode(int dim, const KG& g, const int32_t* d_boxes, int64_t n, uint64_
   bool b = false;
   FR_TRY(read_bad(bad, &b, s, err));
   if (b) return set_error(err, FR_EINVAL, "box with depth/anchor out of range or misaligned");
+  return 0;
+}
+
+int tree_complete(int dim, const KG& g, int Dmin, double L, const double* d_pts, int64_t n,
+                  Buf<uint64_t>& out, int64_t* n_out, Alloc& A, cudaStream_t s, Err* err) {
+  Scratch S(&A);
+  int64_t nn = n > 0 ? n : 1;
+  uint64_t* keys = S.get<uint64_t>(nn);
+  uint64_t* tmp = S.get<uint64_t>(nn);
+  uint64_t* seeds = S.get<uint64_t>(nn);
+  int32_t* c1 = S.get<int32_t>(nn + 1);
+  int64_t* o1 = S.get<int64_t>(nn + 1);
+  int64_t* nS = S.get<int64_t>(1);
+  int64_t* tot = S.get<int64_t>(1);
+  if (!keys || !tmp || !seeds || !c1 || !o1 || !nS || !tot)
+    return set_error(err, FR_ENOMEM, "completion scratch");
+  if (n > 0) {
+    DIM_DISPATCH(dim, (k_pts_encode<D_><<<nblk(n), TB, 0, s>>>(d_pts, n, L, g, keys)));
+    FR_LAUNCH_CHECK(err);
+    FR_TRY(radix_sort_keys(keys, tmp, n, dim * g.Dmax + g.mb, S, s, err));
+    // unique seeds (all at depth Dmax, so linearisation only removes duplicates)
+    DIM_DISPATCH(dim, (k_lin_count<D_><<<nblk(n), TB, 0, s>>>(keys, n, g, c1)));
+    FR_LAUNCH_CHECK(err);
+    FR_TRY(scan_counts(c1, o1, n, nS, S, s, err));
+    k_compact<<<nblk(n), TB, 0, s>>>(keys, c1, o1, n, seeds);
+    FR_LAUNCH_CHECK(err);
+  } else {
+    FR_CUDA(err, cudaMemsetAsync(nS, 0, 8, s));
+  }
+  int64_t ncap = n;  // gaps 0..nS with nS <= n
+  DIM_DISPATCH(dim, (k_gap_count<D_><<<nblk(ncap + 1), TB, 0, s>>>(seeds, nS, ncap, g, Dmin, c1)));
+  FR_LAUNCH_CHECK(err);
+  FR_TRY(scan_counts(c1, o1, ncap + 1, tot, S, s, err));
+  FR_TRY(read_i64(tot, n_out, s, err));
+  FR_TRY(out.ensure(A, size_t(*n_out)));
+  DIM_DISPATCH(dim, (k_gap_write<D_><<<nblk(ncap + 1), TB, 0, s>>>(seeds, nS, ncap, g, Dmin, o1, out.p)));
+  FR_LAUNCH_CHECK(err);
   return 0;
 }
 

@@ -74,7 +74,7 @@ EXPORTS = ["fr_mesh_init", "fr_mesh_free", "fr_step", "fr_run", "fr_adapt", "fr_
            "fr_set_exact", "fr_set_time", "fr_get_info", "fr_last_error", "fr_morton_encode",
            "fr_keys_sort", "fr_keys_linearise", "fr_tree_balance", "fr_tree_adapt", "fr_tree_map",
            "fr_tree_conn", "fr_profile_enable", "fr_profile_read", "fr_kernel_launches",
-           "fr_keys_sort_noalloc"]
+           "fr_keys_sort_noalloc", "fr_tree_complete"]
 NOALLOC_SORT_MAX_KEYS = 1 << 18
 
 
@@ -119,6 +119,8 @@ def load(build_if_missing: bool = True):
     lib.fr_tree_balance.argtypes = [C.c_int, C.c_int, vp, i64, vp, i64, C.POINTER(i64), vp]
     lib.fr_tree_adapt.argtypes = [C.c_int, C.c_int, C.c_int, vp, vp, i64, vp, i64, C.POINTER(i64), vp]
     lib.fr_tree_map.argtypes = [C.c_int, C.c_int, vp, i64, vp, i64, vp, vp, vp]
+    lib.fr_tree_complete.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, vp, i64, vp, i64,
+                                     C.POINTER(i64), vp]
     lib.fr_tree_conn.argtypes = [C.c_int, C.c_int, vp, i64, vp, vp, vp, vp]
     lib.fr_profile_enable.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, C.POINTER(FRProfile)]
@@ -411,6 +413,16 @@ def tree_adapt(dim, Dbase, Dmax, keys, flags, stream=None):
     f = _dev(np.asarray(flags, dtype=np.int8), torch.int8)
     return _grow_call(load().fr_tree_adapt, max(16, 2 * k.numel()), dim, Dbase, Dmax,
                       C.c_void_p(k.data_ptr()), C.c_void_p(f.data_ptr()), k.numel(),
+                      tail=(_stream_handle(stream),))
+
+
+def tree_complete(dim, Dmin, Dmax, L, pts, stream=None):
+    """Tree completion from points (host array or CUDA tensor [n][dim]); returns sorted keys."""
+    torch = _torch()
+    pt = _dev(np.asarray(pts, dtype=np.float64).reshape(-1, dim) if not isinstance(pts, torch.Tensor)
+              else pts, torch.float64)
+    return _grow_call(load().fr_tree_complete, max(16, 4 * pt.shape[0] + (1 << (dim * Dmin))),
+                      dim, Dmin, Dmax, C.c_double(L), C.c_void_p(pt.data_ptr()), pt.shape[0],
                       tail=(_stream_handle(stream),))
 
 

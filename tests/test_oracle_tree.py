@@ -218,3 +218,43 @@ def test_adapt_and_map(dim, Dbase, Dmax, seed):
             # coarsening only where all siblings were flagged -1 and above Dbase
             assert all(flags[src[j] + c] == -1 for c in range(1 << dim))
             assert b[0] >= Dbase
+
+
+def _point_cells(dim, Dmax, L, pts):
+    side = 1 << Dmax
+    cells = set()
+    for p in pts:
+        c = [min(side - 1, max(0, int(np.floor(p[a] / L * side)))) for a in range(dim)]
+        cells.add((Dmax, c[0], c[1], c[2] if dim == 3 else 0))
+    return cells
+
+
+@pytest.mark.parametrize("dim,Dmin,Dmax,npts,seed", [(2, 2, 6, 40, 1), (2, 0, 7, 25, 2), (3, 1, 4, 30, 3),
+                                                     (3, 2, 5, 12, 4)])
+def test_tree_complete_properties(dim, Dmin, Dmax, npts, seed):
+    # Sec. 3.1: the completed tree covers the domain, keeps every point cell as a leaf, stays at or
+    # below Dmin, and is the coarsest such tree (no leaf could be merged into its parent)
+    L = 3.0
+    pts = (W.random_uniform(npts * dim, seed).reshape(npts, dim)) * L
+    keys = O.tree_complete(dim, Dmin, Dmax, L, pts)
+    boxes = [tuple(b) for b in O.morton_decode(dim, Dmax, keys)]
+    assert np.all(np.diff(keys.astype(np.float64)) > 0)
+    assert brute.volume(dim, Dmax, boxes) == (1 << Dmax) ** dim
+    cells = _point_cells(dim, Dmax, L, pts)
+    bset = set(boxes)
+    assert cells <= bset
+    assert all(b[0] >= Dmin for b in boxes)
+    for b in boxes:
+        if b in cells:
+            continue
+        w = 1 << (Dmax - b[0] + 1)
+        par = (b[0] - 1, b[1] // w * w, b[2] // w * w, b[3] // w * w if dim == 3 else 0)
+        assert par[0] < Dmin or any(brute.contains(Dmax, par, c) for c in cells), b
+
+
+def test_tree_complete_closed_forms():
+    # no points: the uniform grid at Dmin; one point: each of the Dmax-Dmin splits adds 2^dim-1
+    for dim in (2, 3):
+        assert len(O.tree_complete(dim, 2, 5, 1.0, np.zeros((0, dim)))) == (1 << (dim * 2))
+        one = O.tree_complete(dim, 2, 5, 1.0, np.full((1, dim), 0.3))
+        assert len(one) == (1 << (dim * 2)) + ((1 << dim) - 1) * (5 - 2)
