@@ -71,7 +71,8 @@ typedef struct {
   int32_t indicator;       /* 0: density gradient eta = h*max|grad rho| (refine if eta >
                               th_refine, coarsen if eta < th_coarsen); 1: analytic centre of
                               Sec. 5.2 (th_refine, th_coarsen are the radii 5 and 6 of the paper);
-                              2: external flags only                                              */
+                              2: external flags only; 3: learned indicator set by
+                              fr_set_learned_indicator, density gradient until weights are set   */
   double th_refine, th_coarsen;
   int32_t precision;       /* arithmetic of the time-step kernels (state, norms and adaptation are
                               always FP64): 0 FP64; 1 FP32 fluxes, operators, traces and common
@@ -159,6 +160,31 @@ int fr_set_exact(fr_mesh* m, double t);
 int fr_set_time(fr_mesh* m, double t);
 int fr_get_info(fr_mesh* m, fr_info* out);
 const char* fr_last_error(const fr_mesh* m);
+
+/* Learned adaptation indicator (an extension: the paper uses an analytic criterion, Sec. 5.2).
+   A per-element MLP maps features -> 3 logits (coarsen, keep, refine): inputs x (IN = 2*3^dim+1) ->
+   64 -> 64 -> 64 -> 3, GELU after each hidden layer; inputs, weights and activations in BF16,
+   every dot product accumulated in FP32.  Parameters: one FP32 array of fr_mlp_param_count(IN)
+   values, [W1 (64xIN, row-major) | b1 | W2 (64x64) | b2 | W3 | b3 | W4 (3x64) | b4].
+   Features of an element (fr_features, BF16 [M][IN]): the state is interpolated to the 3^dim
+   Gauss-Legendre points of order 3 (so one network serves every degree p); there density and
+   pressure give 100*(rho_i - mean rho)/mean rho and 100*(p_i - mean p)/mean p, then
+   (D - Dbase)/max(1, Dmax - Dbase).
+   Labels are classes -1/0/+1 (coarsen/keep/refine), int8.  class_w = {w_coarsen, w_keep, w_refine,
+   1/sum_batch w_label}: the loss is sum_b w_b CE_b * class_w[3] (weighted mean cross-entropy).
+   fr_mlp_train_step performs one Adam step (beta 0.9/0.999, eps 1e-8; d_m, d_v the moment arrays,
+   step counts from 0) in place on d_params; d_loss (device, may be NULL) receives the batch loss.
+   fr_mlp_grad returns the gradient of that loss instead.  Device pointers throughout. */
+int fr_mlp_param_count(int in_dim);
+int fr_features(fr_mesh* m, void* d_X_bf16, int64_t cap, int32_t* in_dim);
+int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n);
+int fr_mlp_forward(int in_dim, const float* d_params, const void* d_X_bf16, int64_t n,
+                   float* d_logits, int8_t* d_flags, void* stream);
+int fr_mlp_grad(int in_dim, const float* d_params, const void* d_X_bf16, const int8_t* d_y,
+                int64_t B, const float* class_w, float* d_grad, float* d_loss, void* stream);
+int fr_mlp_train_step(int in_dim, float* d_params, float* d_m, float* d_v, int64_t step,
+                      const void* d_X_bf16, const int8_t* d_y, int64_t B, const float* class_w,
+                      float lr, float* d_loss, void* stream);
 
 /* Measurement.  With profiling on, every interface and element kernel launched by fr_step,
    fr_run and fr_rhs is bracketed by CUDA events on the mesh's stream; fr_profile_read

@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "fr_internal.cuh"
+#include "fr_mlp.cuh"
 #include "fr_solver.cuh"
 
 using namespace frg;
@@ -31,6 +32,8 @@ struct fr_mesh {
   int64_t n_conf = 0, n_hang = 0;
   Buf<double> norm_part, norm_out;
   Buf<unsigned long long> dmax;
+  Buf<float> mlp_params;  // learned indicator weights (FP32 master copy), empty if none
+  int64_t mlp_n = 0;
   // measurement: event pairs around interface (kind 0) and element (kind 1) launches
   struct Rec {
     int kind;
@@ -107,7 +110,7 @@ int check_cfg(const fr_config* c, Err* err) {
     return set_error(err, FR_EINVAL, "L, gamma, rho_inf, p_inf must be positive (gamma > 1)");
   if (c->nvort < 0 || c->nvort > 16 || (c->nvort > 0 && !c->vort))
     return set_error(err, FR_EINVAL, "nvort must be in 0..16 with a vortex array");
-  if (c->indicator < 0 || c->indicator > 2) return set_error(err, FR_EINVAL, "bad indicator");
+  if (c->indicator < 0 || c->indicator > 3) return set_error(err, FR_EINVAL, "bad indicator");
   if (c->precision < 0 || c->precision > 2) return set_error(err, FR_EINVAL, "precision must be 0, 1 or 2");
   if (!(c->dt > 0) && !(c->cfl > 0)) return set_error(err, FR_EINVAL, "need dt > 0 or cfl > 0");
   return 0;
@@ -249,7 +252,18 @@ int compute_flags(fr_mesh* m, double* eta) {
     FR_CUDA(&m->err, cudaMemsetAsync(m->flags.p, 0, size_t(m->M), m->stream));
     return 0;
   }
-  return launch_indicator(m->dim, m->p, m->cfg.indicator, m->cfg.th_refine, m->cfg.th_coarsen,
+  if (m->cfg.indicator == 3 && m->mlp_n > 0 && !eta) {
+    // learned indicator: features of the current state, then the MLP's argmax
+    int in = mlp_in_dim(m->dim);
+    Scratch Sc(&m->A);
+    void* X = Sc.get<uint16_t>(size_t(m->M) * in);
+    if (!X) return set_error(&m->err, FR_ENOMEM, "feature scratch");
+    FR_TRY(mlp_features(m->dim, m->p, m->u.p, m->keys.p, m->M, m->g, m->cfg.Dbase, m->cfg.gamma,
+                        m->ops, X, m->stream, &m->err));
+    return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->stream, &m->err);
+  }
+  // density gradient (indicator 0, and the fallback of the learned indicator) or analytic centre
+  return launch_indicator(m->dim, m->p, m->cfg.indicator == 1 ? 1 : 0, m->cfg.th_refine, m->cfg.th_coarsen,
                           m->t, m->keys.p, m->M, m->g, m->prob, m->ops, m->u.p, m->flags.p, eta,
                           m->stream, &m->err);
 }
@@ -449,6 +463,7 @@ void free_all(fr_mesh* m) {
   m->norm_part.release(m->A);
   m->norm_out.release(m->A);
   m->dmax.release(m->A);
+  m->mlp_params.release(m->A);
   m->A.release_cache();
   // blocks still handed out (none after a clean release) go back to the allocator as well
   auto live = m->cache.live;
@@ -710,6 +725,71 @@ int fr_profile_read(fr_mesh* m, fr_profile* out) {
 }
 
 int64_t fr_kernel_launches(void) { return launch_counter(); }
+
+// ---- learned adaptation indicator ----
+
+int fr_mlp_param_count(int in_dim) {
+  if (in_dim < 1 || in_dim > 4096) return set_error(global_err(), FR_EINVAL, "bad input width");
+  return mlp_param_count(in_dim);
+}
+
+int fr_features(fr_mesh* m, void* d_X, int64_t cap, int32_t* in_dim) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  int in = mlp_in_dim(m->dim);
+  if (in_dim) *in_dim = in;
+  if (!d_X) return 0;
+  if (cap < m->M * in) return set_error(&m->err, FR_EOVERFLOW, "capacity below M*in_dim");
+  FR_TRY(mlp_features(m->dim, m->p, m->u.p, m->keys.p, m->M, m->g, m->cfg.Dbase, m->cfg.gamma,
+                      m->ops, d_X, m->stream, &m->err));
+  FR_CUDA(&m->err, cudaStreamSynchronize(m->stream));
+  return 0;
+}
+
+int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n) {
+  if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  if (!host_params || n == 0) {
+    m->mlp_n = 0;  // back to the density-gradient indicator
+    return 0;
+  }
+  if (n != mlp_param_count(mlp_in_dim(m->dim)))
+    return set_error(&m->err, FR_EINVAL, "parameter count does not match the feature width");
+  FR_TRY(m->mlp_params.ensure(m->A, size_t(n)));
+  FR_TRY(host_copy(&m->err, m->mlp_params.p, host_params, size_t(n) * 4, cudaMemcpyHostToDevice, m->stream));
+  m->mlp_n = n;
+  return 0;
+}
+
+int fr_mlp_forward(int in_dim, const float* d_params, const void* d_X, int64_t n, float* d_logits,
+                   int8_t* d_flags, void* stream) {
+  if (in_dim < 1 || in_dim > 4096 || n < 0) return set_error(global_err(), FR_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  FR_TRY(mlp_forward(d_params, in_dim, d_X, n, d_logits, d_flags, s, global_err()));
+  FR_CUDA(global_err(), cudaStreamSynchronize(s));
+  return 0;
+}
+
+int fr_mlp_grad(int in_dim, const float* d_params, const void* d_X, const int8_t* d_y, int64_t B,
+                const float* class_w, float* d_grad, float* d_loss, void* stream) {
+  if (in_dim < 1 || in_dim > 4096 || B <= 0 || !class_w)
+    return set_error(global_err(), FR_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Alloc A{nullptr, s, global_err()};
+  FR_TRY(mlp_grad(d_params, in_dim, d_X, d_y, B, class_w, d_grad, d_loss, A, s, global_err()));
+  FR_CUDA(global_err(), cudaStreamSynchronize(s));
+  return 0;
+}
+
+int fr_mlp_train_step(int in_dim, float* d_params, float* d_m, float* d_v, int64_t step,
+                      const void* d_X, const int8_t* d_y, int64_t B, const float* class_w, float lr,
+                      float* d_loss, void* stream) {
+  if (in_dim < 1 || in_dim > 4096 || B <= 0 || !class_w || step < 0)
+    return set_error(global_err(), FR_EINVAL, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Alloc A{nullptr, s, global_err()};
+  FR_TRY(mlp_train_step(d_params, d_m, d_v, step, in_dim, d_X, d_y, B, class_w, lr, d_loss, A, s,
+                        global_err()));
+  return 0;
+}
 
 // ---- tree primitives on caller-owned device arrays ----
 

@@ -1,0 +1,441 @@
+// fr_mlp.cu -- learned adaptation indicator: a per-element MLP that predicts the density-gradient
+// indicator a few steps ahead (refine / keep / coarsen), so adaptation can run less often.
+//
+// Network: x (IN inputs) -> 64 -> 64 -> 64 -> 3 logits, GELU after the three hidden layers.
+// Inputs, weights and activations are stored in BF16; every dot product accumulates in FP32.
+// Parameters are one FP32 array (the optimiser's master copy), laid out
+//   [W1 (64 x IN) | b1 (64) | W2 (64 x 64) | b2 | W3 (64 x 64) | b3 | W4 (3 x 64) | b4 (3)].
+// Features of an element: density and pressure at the 3^dim Gauss-Legendre points of order 3
+// (interpolated from the element's polynomial, so the same network serves every degree), as
+// relative deviations from their means scaled by 100 (a 1% variation is 1.0), then the depth as
+// (D - Dbase) / max(1, Dmax - Dbase): IN = 2*3^dim + 1 inputs (19 in 2D, 55 in 3D).
+//
+// The contractions are 64 wide and cost about 12k multiply-adds per element, well under 0.1% of a
+// time step of the FR solver for the same element, so they run on the CUDA cores (FP32 FMA on
+// BF16-rounded operands); the weights sit in shared memory and are read by broadcast.
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "fr_internal.cuh"
+#include "fr_mlp.cuh"
+
+namespace frg {
+
+namespace {
+
+constexpr int H = MLP_HIDDEN;
+constexpr int NOUT = 3;
+constexpr int MLP_T = 128;  // threads (samples) per block
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// GELU with the exact erf form and its derivative
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+struct Lay {
+  int in;
+  int oW1, ob1, oW2, ob2, oW3, ob3, oW4, ob4, total;
+};
+__host__ __device__ inline Lay lay(int in) {
+  Lay L;
+  L.in = in;
+  L.oW1 = 0;
+  L.ob1 = L.oW1 + H * in;
+  L.oW2 = L.ob1 + H;
+  L.ob2 = L.oW2 + H * H;
+  L.oW3 = L.ob2 + H;
+  L.ob3 = L.oW3 + H * H;
+  L.oW4 = L.ob3 + H;
+  L.ob4 = L.oW4 + NOUT * H;
+  L.total = L.ob4 + NOUT;
+  return L;
+}
+
+// features from the FP64 state: the conserved variables are interpolated from the element's own
+// points to the 3 Gauss-Legendre points per axis (I3 = 3 x n Lagrange matrix), where density and
+// pressure are taken
+struct I3Mat {
+  double m[3][NPMAX];
+};
+
+template <int DIM, int NP>
+__global__ void k_features(const double* __restrict__ u, const uint64_t* __restrict__ keys,
+                           int64_t M, KG g, int Dbase, double gamma, const __grid_constant__ I3Mat I3,
+                           __nv_bfloat16* __restrict__ X) {
+  constexpr int N = DIM == 2 ? NP * NP : NP * NP * NP;
+  constexpr int S = DIM == 2 ? 9 : 27;  // sample points
+  constexpr int NV = DIM + 2, IN = 2 * S + 1;
+  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M) return;
+  const double* q = u + e * NV * N;
+  double rho[S], pr[S], rm = 0.0, pm = 0.0;
+  for (int t = 0; t < S; ++t) {
+    int s0 = t % 3, s1 = (t / 3) % 3, s2 = DIM == 3 ? t / 9 : 0;
+    double qv[NV];
+    for (int v = 0; v < NV; ++v) {
+      double acc = 0.0;
+      for (int i = 0; i < N; ++i) {
+        int i0 = i % NP, i1 = (i / NP) % NP, i2 = DIM == 3 ? i / (NP * NP) : 0;
+        double w = I3.m[s0][i0] * I3.m[s1][i1];
+        if (DIM == 3) w *= I3.m[s2][i2];
+        acc += w * q[v * N + i];
+      }
+      qv[v] = acc;
+    }
+    double m2 = 0.0;
+    for (int b = 0; b < DIM; ++b) m2 += qv[1 + b] * qv[1 + b];
+    double p = (gamma - 1.0) * (qv[NV - 1] - 0.5 * m2 / qv[0]);
+    rho[t] = qv[0];
+    pr[t] = p;
+    rm += qv[0];
+    pm += p;
+  }
+  rm /= S;
+  pm /= S;
+  __nv_bfloat16* x = X + e * IN;
+  for (int t = 0; t < S; ++t) {
+    x[t] = __float2bfloat16_rn(float(100.0 * (rho[t] - rm) / rm));
+    x[S + t] = __float2bfloat16_rn(float(100.0 * (pr[t] - pm) / pm));
+  }
+  int span = g.Dmax - Dbase > 0 ? g.Dmax - Dbase : 1;
+  x[2 * S] = __float2bfloat16_rn(float(g.depth(keys[e]) - Dbase) / float(span));
+}
+
+// shared-memory copy of the BF16-rounded weights as floats
+__device__ void load_weights(const float* __restrict__ P, int total, float* sw) {
+  for (int k = threadIdx.x; k < total; k += blockDim.x) sw[k] = bf16r(P[k]);
+}
+
+// first layer: z[i] = b[i] + sum_k W[i][k] x_k, x read from the BF16 input row
+__device__ __forceinline__ void layer_in(const float* W, const float* b, const __nv_bfloat16* x,
+                                         int in, float (&z)[H]) {
+#pragma unroll
+  for (int i = 0; i < H; ++i) z[i] = b[i];
+  for (int k = 0; k < in; ++k) {
+    float xk = __bfloat162float(x[k]);
+#pragma unroll
+    for (int i = 0; i < H; ++i) z[i] = fmaf(W[i * in + k], xk, z[i]);
+  }
+}
+// hidden layer: z[i] = b[i] + sum_k W[i][k] a_k
+__device__ __forceinline__ void layer_h(const float* W, const float* b, const float (&a)[H],
+                                        float (&z)[H]) {
+#pragma unroll
+  for (int i = 0; i < H; ++i) z[i] = b[i];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+#pragma unroll
+    for (int i = 0; i < H; ++i) z[i] = fmaf(W[i * H + k], a[k], z[i]);
+  }
+}
+__device__ __forceinline__ void act(const float (&z)[H], float (&a)[H]) {
+#pragma unroll
+  for (int i = 0; i < H; ++i) a[i] = bf16r(gelu(z[i]));
+}
+__device__ __forceinline__ void layer_out(const float* W, const float* b, const float (&a)[H],
+                                          float (&z)[NOUT]) {
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) {
+    float t = b[c];
+#pragma unroll
+    for (int k = 0; k < H; ++k) t = fmaf(W[c * H + k], a[k], t);
+    z[c] = t;
+  }
+}
+
+__global__ void __launch_bounds__(MLP_T) k_mlp_forward(const float* __restrict__ P, int in,
+                                                       const __nv_bfloat16* __restrict__ X,
+                                                       int64_t n, float* __restrict__ logits,
+                                                       int8_t* __restrict__ flags) {
+  extern __shared__ float sw[];
+  const Lay L = lay(in);
+  load_weights(P, L.total, sw);
+  __syncthreads();
+  int64_t b = int64_t(blockIdx.x) * MLP_T + threadIdx.x;
+  if (b >= n) return;
+  float z[H], a[H], o[NOUT];
+  layer_in(sw + L.oW1, sw + L.ob1, X + b * in, in, z);
+  act(z, a);
+  layer_h(sw + L.oW2, sw + L.ob2, a, z);
+  act(z, a);
+  layer_h(sw + L.oW3, sw + L.ob3, a, z);
+  act(z, a);
+  layer_out(sw + L.oW4, sw + L.ob4, a, o);
+  if (logits)
+    for (int c = 0; c < NOUT; ++c) logits[b * NOUT + c] = o[c];
+  if (flags) {
+    int best = 0;
+    for (int c = 1; c < NOUT; ++c)
+      if (o[c] > o[best]) best = c;
+    flags[b] = int8_t(best - 1);  // class 0 coarsen, 1 keep, 2 refine
+  }
+}
+
+// training, per sample: forward, weighted softmax cross-entropy, backward to every layer's
+// pre-activation gradient.  Stores the inputs of every layer (A0..A3), the pre-activations
+// (Z1..Z3) and the gradients (D1..D4) for the weight-gradient reduction, and the sample's loss.
+__global__ void __launch_bounds__(MLP_T) k_mlp_fwd_bwd(const float* __restrict__ P, int in,
+                                                       const __nv_bfloat16* __restrict__ X,
+                                                       const int8_t* __restrict__ y, int64_t B,
+                                                       float cw0, float cw1, float cw2, float inv_wsum,
+                                                       float* __restrict__ A, float* __restrict__ Z,
+                                                       float* __restrict__ D, float* __restrict__ loss) {
+  extern __shared__ float sw[];
+  const Lay L = lay(in);
+  load_weights(P, L.total, sw);
+  __syncthreads();
+  int64_t b = int64_t(blockIdx.x) * MLP_T + threadIdx.x;
+  if (b >= B) return;
+  const int64_t HA = B * H;
+  float* A0 = A;  // B x in, then A1..A3 (B x 64 each)
+  float* A1 = A + B * in;
+  float* A2 = A1 + HA;
+  float* A3 = A2 + HA;
+  float* Z1 = Z;
+  float* Z2 = Z + HA;
+  float* Z3 = Z2 + HA;
+  float* D1 = D;  // B x 64 each, then D4: B x 3
+  float* D2 = D1 + HA;
+  float* D3 = D2 + HA;
+  float* D4 = D3 + HA;
+  const __nv_bfloat16* x = X + b * in;
+  for (int k = 0; k < in; ++k) A0[b * in + k] = __bfloat162float(x[k]);
+  float z[H], a[H], o[NOUT];
+  layer_in(sw + L.oW1, sw + L.ob1, x, in, z);
+  act(z, a);
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    Z1[b * H + i] = z[i];
+    A1[b * H + i] = a[i];
+  }
+  layer_h(sw + L.oW2, sw + L.ob2, a, z);
+  act(z, a);
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    Z2[b * H + i] = z[i];
+    A2[b * H + i] = a[i];
+  }
+  layer_h(sw + L.oW3, sw + L.ob3, a, z);
+  act(z, a);
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    Z3[b * H + i] = z[i];
+    A3[b * H + i] = a[i];
+  }
+  layer_out(sw + L.oW4, sw + L.ob4, a, o);
+  // softmax cross-entropy with class weights, normalised by the batch's total weight
+  int cls = int(y[b]) + 1;
+  float w = cls == 0 ? cw0 : (cls == 1 ? cw1 : cw2);
+  float mx = fmaxf(o[0], fmaxf(o[1], o[2]));
+  float e0 = expf(o[0] - mx), e1 = expf(o[1] - mx), e2 = expf(o[2] - mx);
+  float sum = e0 + e1 + e2;
+  float pz[NOUT] = {e0 / sum, e1 / sum, e2 / sum};
+  loss[b] = -w * inv_wsum * logf(pz[cls]);
+  float d4[NOUT];
+#pragma unroll
+  for (int c = 0; c < NOUT; ++c) {
+    d4[c] = w * inv_wsum * (pz[c] - (c == cls ? 1.f : 0.f));
+    D4[b * NOUT + c] = d4[c];
+  }
+  // backward: d3 = (W4^T d4) * gelu'(z3), d2 = (W3^T d3) * gelu'(z2), d1 = (W2^T d2) * gelu'(z1)
+  float d[H], g[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    float t = 0.f;
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) t = fmaf(sw[L.oW4 + c * H + k], d4[c], t);
+    d[k] = t * gelu_d(Z3[b * H + k]);
+    D3[b * H + k] = d[k];
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) g[k] = 0.f;
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fmaf(sw[L.oW3 + i * H + k], d[i], g[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    d[k] = g[k] * gelu_d(Z2[b * H + k]);
+    D2[b * H + k] = d[k];
+    g[k] = 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+#pragma unroll
+    for (int k = 0; k < H; ++k) g[k] = fmaf(sw[L.oW2 + i * H + k], d[i], g[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < H; ++k) D1[b * H + k] = g[k] * gelu_d(Z1[b * H + k]);
+}
+
+// weight gradients, one thread per parameter, summing the batch in index order (deterministic)
+__global__ void k_mlp_wgrad(int in, int64_t B, const float* __restrict__ A, const float* __restrict__ D,
+                            float* __restrict__ G) {
+  const Lay L = lay(in);
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.total) return;
+  const int64_t HA = B * H;
+  const float* A0 = A;
+  const float* A1 = A + B * in;
+  const float* A2 = A1 + HA;
+  const float* A3 = A2 + HA;
+  const float* D1 = D;
+  const float* D2 = D1 + HA;
+  const float* D3 = D2 + HA;
+  const float* D4 = D3 + HA;
+  const float *Ad = nullptr, *Dd = nullptr;
+  int nin = 0, nout = H, i = 0, k = -1;
+  if (t < L.ob1) { Ad = A0; Dd = D1; nin = in; i = (t - L.oW1) / in; k = (t - L.oW1) % in; }
+  else if (t < L.oW2) { Dd = D1; i = t - L.ob1; }
+  else if (t < L.ob2) { Ad = A1; Dd = D2; nin = H; i = (t - L.oW2) / H; k = (t - L.oW2) % H; }
+  else if (t < L.oW3) { Dd = D2; i = t - L.ob2; }
+  else if (t < L.ob3) { Ad = A2; Dd = D3; nin = H; i = (t - L.oW3) / H; k = (t - L.oW3) % H; }
+  else if (t < L.oW4) { Dd = D3; i = t - L.ob3; }
+  else if (t < L.ob4) { Ad = A3; Dd = D4; nin = H; nout = NOUT; i = (t - L.oW4) / H; k = (t - L.oW4) % H; }
+  else { Dd = D4; nout = NOUT; i = t - L.ob4; }
+  float s = 0.f;
+  if (k >= 0) {
+    for (int64_t b = 0; b < B; ++b) s = fmaf(Dd[b * nout + i], Ad[b * nin + k], s);
+  } else {
+    for (int64_t b = 0; b < B; ++b) s += Dd[b * nout + i];
+  }
+  G[t] = s;
+}
+
+// Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr mhat / (sqrt(vhat) + eps)
+__global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ G, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  float g = G[t];
+  float mt = b1 * m[t] + (1.f - b1) * g;
+  float vt = b2 * v[t] + (1.f - b2) * g * g;
+  m[t] = mt;
+  v[t] = vt;
+  P[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+}
+
+// deterministic sum of the per-sample losses (one block, fixed order)
+__global__ void k_sum(const float* __restrict__ x, int64_t n, float* __restrict__ out) {
+  __shared__ float s[256];
+  float a = 0.f;
+  for (int64_t i = threadIdx.x; i < n; i += 256) a += x[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (int(threadIdx.x) < st) s[threadIdx.x] += s[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+size_t fwd_smem(int in) { return sizeof(float) * size_t(lay(in).total); }
+
+}  // namespace
+
+int mlp_param_count(int in) { return lay(in).total; }
+
+int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float* d_logits,
+                int8_t* d_flags, cudaStream_t s, Err* err) {
+  if (n <= 0) return 0;
+  size_t sm = fwd_smem(in);
+  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  k_mlp_forward<<<unsigned((n + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
+      d_params, in, static_cast<const __nv_bfloat16*>(d_X), n, d_logits, d_flags);
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int mlp_in_dim(int dim) { return 2 * (dim == 2 ? 9 : 27) + 1; }
+
+int mlp_features(int dim, int p, const double* u, const uint64_t* keys, int64_t M, const KG& g,
+                 int Dbase, double gamma, const DevOps& ops, void* d_X, cudaStream_t s, Err* err) {
+  if (M <= 0) return 0;
+  // Lagrange basis of the element's points evaluated at the 3-point Gauss-Legendre nodes
+  I3Mat I3{};
+  const double g3[3] = {-std::sqrt(0.6), 0.0, std::sqrt(0.6)};
+  int np = p + 1;
+  for (int t = 0; t < 3; ++t)
+    for (int j = 0; j < np; ++j) {
+      double pr = 1.0;
+      for (int k = 0; k < np; ++k)
+        if (k != j) pr *= (g3[t] - ops.x[k]) / (ops.x[j] - ops.x[k]);
+      I3.m[t][j] = pr;
+    }
+  unsigned nb = unsigned((M + 127) / 128);
+  __nv_bfloat16* X = static_cast<__nv_bfloat16*>(d_X);
+#define FEAT(D_, N_) k_features<D_, N_><<<nb, 128, 0, s>>>(u, keys, M, g, Dbase, gamma, I3, X)
+  if (dim == 2) {
+    if (np == 2) FEAT(2, 2); else if (np == 3) FEAT(2, 3); else if (np == 4) FEAT(2, 4); else FEAT(2, 5);
+  } else {
+    if (np == 2) FEAT(3, 2); else if (np == 3) FEAT(3, 3); else if (np == 4) FEAT(3, 4); else FEAT(3, 5);
+  }
+#undef FEAT
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+int mlp_train_step(float* d_params, float* d_m, float* d_v, int64_t step, int in, const void* d_X,
+                   const int8_t* d_y, int64_t B, const float* cw, float lr, float* d_loss,
+                   Alloc& A, cudaStream_t s, Err* err) {
+  if (B <= 0) return set_error(err, FR_EINVAL, "empty batch");
+  const Lay L = lay(in);
+  Scratch S(&A);
+  float* acts = S.get<float>(size_t(B) * (in + 3 * H));
+  float* pre = S.get<float>(size_t(B) * 3 * H);
+  float* dels = S.get<float>(size_t(B) * (3 * H + NOUT));
+  float* G = S.get<float>(L.total);
+  float* ls = S.get<float>(B);
+  if (!acts || !pre || !dels || !G || !ls) return set_error(err, FR_ENOMEM, "training scratch");
+  // class weights normalised by the batch's total weight: computed by the caller as cw[0..2]
+  // and cw[3] = 1 / sum_b w_{y_b}
+  size_t sm = fwd_smem(in);
+  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  k_mlp_fwd_bwd<<<unsigned((B + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
+      d_params, in, static_cast<const __nv_bfloat16*>(d_X), d_y, B, cw[0], cw[1], cw[2], cw[3], acts,
+      pre, dels, ls);
+  FR_LAUNCH_CHECK(err);
+  k_mlp_wgrad<<<unsigned((L.total + 127) / 128), 128, 0, s>>>(in, B, acts, dels, G);
+  FR_LAUNCH_CHECK(err);
+  const float b1 = 0.9f, b2 = 0.999f;
+  float c1 = 1.f - std::pow(b1, float(step + 1)), c2 = 1.f - std::pow(b2, float(step + 1));
+  k_adam<<<unsigned((L.total + 255) / 256), 256, 0, s>>>(d_params, d_m, d_v, G, L.total, lr, b1, b2,
+                                                         1e-8f, c1, c2);
+  FR_LAUNCH_CHECK(err);
+  if (d_loss) {
+    k_sum<<<1, 256, 0, s>>>(ls, B, d_loss);
+    FR_LAUNCH_CHECK(err);
+  }
+  return 0;
+}
+
+int mlp_grad(const float* d_params, int in, const void* d_X, const int8_t* d_y, int64_t B,
+             const float* cw, float* d_grad, float* d_loss, Alloc& A, cudaStream_t s, Err* err) {
+  if (B <= 0) return set_error(err, FR_EINVAL, "empty batch");
+  const Lay L = lay(in);
+  Scratch S(&A);
+  float* acts = S.get<float>(size_t(B) * (in + 3 * H));
+  float* pre = S.get<float>(size_t(B) * 3 * H);
+  float* dels = S.get<float>(size_t(B) * (3 * H + NOUT));
+  float* ls = S.get<float>(B);
+  if (!acts || !pre || !dels || !ls) return set_error(err, FR_ENOMEM, "gradient scratch");
+  size_t sm = fwd_smem(in);
+  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  k_mlp_fwd_bwd<<<unsigned((B + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
+      d_params, in, static_cast<const __nv_bfloat16*>(d_X), d_y, B, cw[0], cw[1], cw[2], cw[3], acts,
+      pre, dels, ls);
+  FR_LAUNCH_CHECK(err);
+  k_mlp_wgrad<<<unsigned((L.total + 127) / 128), 128, 0, s>>>(in, B, acts, dels, d_grad);
+  FR_LAUNCH_CHECK(err);
+  k_sum<<<1, 256, 0, s>>>(ls, B, d_loss);
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+}  // namespace frg

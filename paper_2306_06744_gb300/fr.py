@@ -74,7 +74,8 @@ EXPORTS = ["fr_mesh_init", "fr_mesh_free", "fr_step", "fr_run", "fr_adapt", "fr_
            "fr_set_exact", "fr_set_time", "fr_get_info", "fr_last_error", "fr_morton_encode",
            "fr_keys_sort", "fr_keys_linearise", "fr_tree_balance", "fr_tree_adapt", "fr_tree_map",
            "fr_tree_conn", "fr_profile_enable", "fr_profile_read", "fr_kernel_launches",
-           "fr_keys_sort_noalloc", "fr_tree_complete"]
+           "fr_keys_sort_noalloc", "fr_tree_complete", "fr_mlp_param_count", "fr_features",
+           "fr_set_learned_indicator", "fr_mlp_forward", "fr_mlp_grad", "fr_mlp_train_step"]
 NOALLOC_SORT_MAX_KEYS = 1 << 18
 
 
@@ -122,6 +123,12 @@ def load(build_if_missing: bool = True):
     lib.fr_tree_complete.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, vp, i64, vp, i64,
                                      C.POINTER(i64), vp]
     lib.fr_tree_conn.argtypes = [C.c_int, C.c_int, vp, i64, vp, vp, vp, vp]
+    lib.fr_mlp_param_count.argtypes = [C.c_int]
+    lib.fr_features.argtypes = [vp, vp, i64, C.POINTER(C.c_int32)]
+    lib.fr_set_learned_indicator.argtypes = [vp, vp, i64]
+    lib.fr_mlp_forward.argtypes = [C.c_int, vp, vp, i64, vp, vp, vp]
+    lib.fr_mlp_grad.argtypes = [C.c_int, vp, vp, vp, i64, vp, vp, vp, vp]
+    lib.fr_mlp_train_step.argtypes = [C.c_int, vp, vp, vp, i64, vp, vp, i64, vp, C.c_float, vp, vp]
     lib.fr_profile_enable.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, C.POINTER(FRProfile)]
     lib.fr_kernel_launches.restype = C.c_int64
@@ -320,6 +327,23 @@ class Mesh:
         self._ck(load().fr_profile_read(self.h, C.byref(o)))
         return {k: getattr(o, k) for k, _ in FRProfile._fields_}
 
+    def features(self):
+        """BF16 features [M][in_dim] of the current state as a CUDA tensor (learned indicator)."""
+        torch = _torch()
+        n_in = C.c_int32()
+        self._ck(load().fr_features(self.h, None, 0, C.byref(n_in)))
+        X = torch.empty((self.M, n_in.value), dtype=torch.bfloat16, device="cuda")
+        self._ck(load().fr_features(self.h, C.c_void_p(X.data_ptr()), X.numel(), None))
+        return X
+
+    def set_learned_indicator(self, params):
+        """Installs MLP weights (FP32 host array) for indicator 3; None restores the fallback."""
+        if params is None:
+            self._ck(load().fr_set_learned_indicator(self.h, None, 0))
+            return
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._ck(load().fr_set_learned_indicator(self.h, _np_ptr(p), p.size))
+
     def conn(self):
         M = self.M
         S = M * 2 * self.dim
@@ -328,6 +352,55 @@ class Mesh:
         sl = np.zeros(S, dtype=np.int8)
         self._ck(load().fr_get_conn(self.h, _np_ptr(nbr), _np_ptr(ft), _np_ptr(sl), S))
         return nbr.reshape(M, -1), ft.reshape(M, -1), sl.reshape(M, -1)
+
+
+def mlp_param_count(in_dim: int) -> int:
+    n = load().fr_mlp_param_count(in_dim)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def _class_w(cw, y):
+    cw = np.asarray(cw, dtype=np.float64)
+    yy = np.asarray(y.cpu().numpy() if hasattr(y, "cpu") else y, dtype=np.int64) + 1
+    wsum = float(cw[yy].sum())
+    return np.array([cw[0], cw[1], cw[2], 1.0 / wsum], dtype=np.float32)
+
+
+def mlp_forward(params, X, stream=None):
+    """Logits [n][3] (CUDA float tensor) of BF16 features X [n][in] with FP32 params (CUDA)."""
+    torch = _torch()
+    n, n_in = X.shape
+    logits = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    flags = torch.empty(n, dtype=torch.int8, device="cuda")
+    _check(load().fr_mlp_forward(n_in, C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()), n,
+                                 C.c_void_p(logits.data_ptr()), C.c_void_p(flags.data_ptr()),
+                                 _stream_handle(stream)))
+    return logits, flags
+
+
+def mlp_grad(params, X, y, class_w, stream=None):
+    torch = _torch()
+    n, n_in = X.shape
+    g = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    cw = _class_w(class_w, y)
+    _check(load().fr_mlp_grad(n_in, C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()),
+                              C.c_void_p(y.data_ptr()), n, _np_ptr(cw), C.c_void_p(g.data_ptr()),
+                              C.c_void_p(loss.data_ptr()), _stream_handle(stream)))
+    return float(loss.item()), g
+
+
+def mlp_train_step(params, m, v, step, X, y, class_w, lr, loss=None, stream=None):
+    """One Adam step in place on `params` (CUDA FP32); X BF16 [B][in], y int8 in {-1,0,1}."""
+    B, n_in = X.shape
+    cw = _class_w(class_w, y)
+    _check(load().fr_mlp_train_step(n_in, C.c_void_p(params.data_ptr()), C.c_void_p(m.data_ptr()),
+                                    C.c_void_p(v.data_ptr()), step, C.c_void_p(X.data_ptr()),
+                                    C.c_void_p(y.data_ptr()), B, _np_ptr(cw), C.c_float(lr),
+                                    C.c_void_p(loss.data_ptr()) if loss is not None else None,
+                                    _stream_handle(stream)))
 
 
 def kernel_launches() -> int:

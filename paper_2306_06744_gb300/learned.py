@@ -1,0 +1,105 @@
+"""Learned adaptation indicator: data generation, training and deployment helpers.
+
+The indicator is a per-element MLP (features of `Mesh.features`, 3 hidden layers of 64, GELU,
+logits for coarsen / keep / refine) that predicts the density-gradient indicator `horizon` steps
+ahead, so that adaptation can run less often.  Every numeric step runs in the library's kernels
+(features, forward, backward, Adam); this module only sequences them.
+
+Labels: from a snapshot of a plain run, a copy of the mesh is advanced `horizon` steps without
+adaptation and the density-gradient indicator of that future state, on the same leaves, is the
+label of each leaf.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import fr
+from . import workloads as W
+
+
+def init_params(in_dim: int, seed: int) -> np.ndarray:
+    """Uniform fan-in scaled initial weights (sqrt(6/fan_in)) and zero biases, from splitmix64."""
+    n = fr.mlp_param_count(in_dim)
+    r = W.random_uniform(n, seed) * 2.0 - 1.0
+    out = np.zeros(n, dtype=np.float32)
+    off = 0
+    for fan_in, rows in ((in_dim, 64), (64, 64), (64, 64), (64, 3)):
+        nw = fan_in * rows
+        out[off:off + nw] = r[off:off + nw] * np.sqrt(6.0 / fan_in)
+        off += nw + rows  # biases stay zero
+    return out
+
+
+def collect_pairs(cfg: dict, snapshots: int, horizon: int = 20, every: int = 10, warmup: int = 0):
+    """Feature/label pairs from a plain run of `cfg` (density-gradient indicator).
+
+    Returns (X, y): CUDA tensors, BF16 [n][in] and int8 [n] in {-1, 0, 1}.
+    """
+    import torch
+    base = dict(cfg, indicator=0)
+    run = fr.Mesh(base)
+    probe = fr.Mesh(dict(base, init_passes=0))
+    for _ in range(warmup):
+        run.step(every)
+        run.adapt()
+    Xs, ys = [], []
+    for _ in range(snapshots):
+        run.step(every)
+        run.adapt()
+        Xs.append(run.features())
+        probe.set_state(run.leaves(), run.state())
+        probe.set_time(run.info()["t"])
+        probe.step(horizon)
+        f, _ = probe.flags()
+        ys.append(torch.from_numpy(f).cuda())
+    run.close()
+    probe.close()
+    return torch.cat(Xs), torch.cat(ys)
+
+
+def class_weights(y) -> np.ndarray:
+    """Inverse-frequency class weights (coarsen, keep, refine), normalised to mean 1."""
+    yy = y.cpu().numpy().astype(np.int64) + 1
+    cnt = np.bincount(yy, minlength=3).astype(np.float64)
+    w = np.where(cnt > 0, cnt.sum() / (3.0 * np.maximum(cnt, 1.0)), 0.0)
+    return w
+
+
+def train(X, y, epochs: int = 5, batch: int = 4096, lr: float = 2e-3, seed: int = 7,
+          class_w=None, log=None):
+    """Adam on the weighted cross-entropy; returns FP32 parameters (numpy) and the loss history."""
+    import torch
+    n, in_dim = X.shape
+    params = torch.from_numpy(init_params(in_dim, seed)).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    cw = class_weights(y) if class_w is None else np.asarray(class_w, dtype=np.float64)
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    hist = []
+    step = 0
+    for ep in range(epochs):
+        perm = np.random.default_rng(seed + 1000 * (ep + 1)).permutation(n)  # seeded shuffle
+        permt = torch.from_numpy(perm).cuda()
+        Xp, yp = X[permt].contiguous(), y[permt].contiguous()
+        tot, nb = 0.0, 0
+        for b0 in range(0, n - batch + 1, batch):
+            fr.mlp_train_step(params, m, v, step, Xp[b0:b0 + batch], yp[b0:b0 + batch], cw, lr, loss)
+            step += 1
+            tot += float(loss.item()) if (nb % 50 == 0) else 0.0
+            nb += 1
+        hist.append(tot / max(1, (nb + 49) // 50))
+        if log:
+            log("epoch %d: loss %.4f" % (ep, hist[-1]))
+    return params.cpu().numpy(), hist
+
+
+def accuracy(params, X, y):
+    """Fraction of samples whose argmax class equals the label, and the confusion matrix."""
+    import torch
+    p = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32)).cuda()
+    _, flags = fr.mlp_forward(p, X)
+    f = flags.cpu().numpy().astype(np.int64) + 1
+    t = y.cpu().numpy().astype(np.int64) + 1
+    conf = np.zeros((3, 3), dtype=np.int64)
+    np.add.at(conf, (t, f), 1)
+    return float((f == t).mean()), conf
