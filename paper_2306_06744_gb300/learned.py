@@ -103,3 +103,73 @@ def accuracy(params, X, y):
     conf = np.zeros((3, 3), dtype=np.int64)
     np.add.at(conf, (t, f), 1)
     return float((f == t).mean()), conf
+
+
+def deploy_run(cfg: dict, steps: int, every: int, params=None) -> dict:
+    """Runs `steps` steps adapting every `every` steps; wall time of steps and adaptations."""
+    import time
+
+    import torch
+    m = fr.Mesh(cfg)
+    if params is not None:
+        m.set_learned_indicator(params)
+    ts = ta = 0.0
+    n_adapt = 0
+    for _ in range(steps // every):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        m.step(every)
+        torch.cuda.synchronize()
+        b = time.perf_counter()
+        m.adapt()
+        torch.cuda.synchronize()
+        c = time.perf_counter()
+        ts += b - a
+        ta += c - b
+        n_adapt += 1
+    nm = m.norms()
+    out = dict(l2_rho=nm["l2_rho"], t=nm["t"], M_final=m.M, steps_s=ts, adapt_s=ta, total_s=ts + ta,
+               adaptations=n_adapt, adaptation_pct=100.0 * ta / (ts + ta))
+    m.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def experiment(steps: int = 120, snapshots: int = 30, log=print) -> dict:
+    """Train on the 3D p=2 tube (labels: the deployment's plain indicator 20 steps ahead), deploy
+    on the four-tube 3D p=3 setup adapting every 30 steps, against the plain indicator every 10."""
+    import time
+
+    import torch
+    cfg4 = W.config("vortex3d_p3_multi")
+    cfg3 = dict(W.config("vortex3d_p2_tube"), precision=2,
+                th_refine=cfg4["th_refine"], th_coarsen=cfg4["th_coarsen"])
+    t0 = time.perf_counter()
+    X, y = collect_pairs(cfg3, snapshots=snapshots, horizon=20, every=10)
+    t_collect = time.perf_counter() - t0
+    n = X.shape[0]
+    ntr = int(0.9 * n)
+    t0 = time.perf_counter()
+    params, hist = train(X[:ntr], y[:ntr], epochs=6, batch=4096, lr=2e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    acc, conf = accuracy(params, X[ntr:], y[ntr:])
+    res = dict(pairs=int(n), collect_s=t_collect, train_s=t_train, loss_history=hist,
+               heldout_accuracy=acc, confusion=conf.tolist())
+    del X, y
+    torch.cuda.empty_cache()
+    res["plain_f64_every10"] = deploy_run(dict(cfg4, precision=0, indicator=0), steps, 10)
+    res["learned_f64_every30"] = deploy_run(dict(cfg4, precision=0, indicator=3), steps, 30, params)
+    res["learned_double_word_every30"] = deploy_run(dict(cfg4, precision=2, indicator=3), steps, 30,
+                                                    params)
+    return res
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    out = experiment()
+    print(json.dumps(out))
+    if len(sys.argv) > 1:
+        with open(sys.argv[1], "w") as fh:
+            json.dump(out, fh, indent=1)
