@@ -338,9 +338,8 @@ __global__ void __launch_bounds__(128) k_stage_t(StageArgs A, const __grid_const
   }
   __syncthreads();
   if (act) {
+    // the per-axis sums are accumulated straight into R (one FMA chain per variable)
     T R[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) R[v] = zero_t<T>();
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       int qf, ia;
@@ -350,20 +349,22 @@ __global__ void __launch_bounds__(128) k_stage_t(StageArgs A, const __grid_const
       const T* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T d = fma_t(ops.gL[ia], Fm[v * NF], ops.gR[ia] * Fp[v * NF]);
+        T d = a == 0 ? ops.gR[ia] * Fp[v * NF] : fma_t(ops.gR[ia], Fp[v * NF], R[v]);
+        d = fma_t(ops.gL[ia], Fm[v * NF], d);
 #pragma unroll
         for (int j = 0; j < NP; ++j) d = fma_t(ops.Dt[ia][j], fa[v * N + line_pt<DIM, NP>(a, qf, j)], d);
-        R[v] = R[v] + d;
+        R[v] = d;
       }
     }
     const double s2 = -sh2[le];
     const int64_t base = (e0 + le) * EU + i;
     if constexpr (!std::is_same<T, ff>::value) {
       // FP64 combination (native FP64 and the mixed FP32 form)
+      const double cs = A.c * s2;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double o = A.b * A.us[base + v * N] + A.c * (s2 * Ar<T>::to_d(R[v]));
-        if (A.a != 0.0) o += A.a * A.un[base + v * N];
+        double o = fma(cs, Ar<T>::to_d(R[v]), A.b * A.us[base + v * N]);
+        if (A.a != 0.0) o = fma(A.a, A.un[base + v * N], o);
         outv[v] = o;
       }
     } else {
