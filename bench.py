@@ -166,7 +166,7 @@ def _traffic_from_profiles(kernel):
     """Per-launch DRAM bytes of `kernel` recorded in profiles/, if the recorded source hash still
     matches the kernel source (otherwise the counters are stale: None)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2306_06744_gb300", "csrc", "fr_solver.cu")
+    src = os.path.join(ROOT, "paper_2306_06744_gb300", "csrc", "fr_kernels.cuh")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):

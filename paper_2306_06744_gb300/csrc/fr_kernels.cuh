@@ -161,9 +161,10 @@ __global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid
   tr[idx] = s;
 }
 
-// interface kernel: blocks [0, nb_conf) do conforming faces (one thread per face point), the
-// others do hanging faces (one block slice per coarse face: Rusanov on every mortar piece, then
-// the coarse side's L2 back-projection, owner-computes, Sec. 4.3)
+// interface kernel: blocks [0, nb_hang) do hanging faces (one block slice per coarse face: Rusanov
+// on every mortar piece, then the coarse side's L2 back-projection, owner-computes, Sec. 4.3), the
+// others conforming faces (one thread per face point).  The heavier hanging blocks come first so
+// that they are not left running alone at the end of the grid.
 template <int DIM, int NP, class T>
 __global__ void __launch_bounds__(128) k_faces_t(FaceArgs A, const __grid_constant__ OpsT<T> ops) {
   using S = Sz<DIM, NP>;
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(128) k_faces_t(FaceArgs A, const __grid_consta
   T* fcomm = static_cast<T*>(A.fcomm);
   const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
   const int tid = threadIdx.x;
-  if (int64_t(blockIdx.x) < A.nb_conf) {
-    int64_t idx = int64_t(blockIdx.x) * 128 + tid;
+  if (int64_t(blockIdx.x) >= A.nb_hang) {
+    int64_t idx = (int64_t(blockIdx.x) - A.nb_hang) * 128 + tid;
     int64_t face = idx / NF;
     int q = int(idx % NF);
     if (face >= A.n_conf) return;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(128) k_faces_t(FaceArgs A, const __grid_consta
     }
     return;
   }
-  const int64_t hb = int64_t(blockIdx.x) - A.nb_conf;
+  const int64_t hb = int64_t(blockIdx.x);
   const int lf = tid / PER, r = tid % PER, s = r / NF, q = r % NF;
   const int64_t hf = hb * FPB + lf;
   const bool act = lf < FPB && hf < A.n_hang;
@@ -450,8 +451,8 @@ int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t 
   int NF = ipow_k(p + 1, dim - 1), PER = (1 << (dim - 1)) * NF;
   int FPB = 128 / PER > 0 ? 128 / PER : 1;
   A.nb_conf = (A.n_conf * NF + 127) / 128;
-  int64_t nb_hang = (A.n_hang + FPB - 1) / FPB;
-  int64_t nb = A.nb_conf + nb_hang;
+  A.nb_hang = (A.n_hang + FPB - 1) / FPB;
+  int64_t nb = A.nb_conf + A.nb_hang;
   if (nb == 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
   FR_NP_DISPATCH(dim, p, (k_faces_t<DD, NN, T><<<unsigned(nb), 128, 0, s>>>(A, ops)));

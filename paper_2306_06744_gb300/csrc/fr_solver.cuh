@@ -11,7 +11,7 @@ struct FaceArgs {
   const int32_t* conf;    // conforming faces: (minus element << 2) | axis
   const int32_t* hang;    // hanging faces: (coarse element << 3) | coarse face
   const int32_t* contrib; // [n_hang][4] fine elements in slot order
-  int64_t n_conf, n_hang, nb_conf;
+  int64_t n_conf, n_hang, nb_conf, nb_hang;
   double gamma;
 };
 
