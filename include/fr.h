@@ -189,7 +189,10 @@ int fr_mlp_train_step(int in_dim, float* d_params, float* d_m, float* d_v, int64
 /* Measurement.  With profiling on, every interface and element kernel launched by fr_step,
    fr_run and fr_rhs is bracketed by CUDA events on the mesh's stream; fr_profile_read
    synchronises, sums the event intervals and returns them with the work those launches did.
-   fr_profile_enable(m, 1) (re)starts the counters, fr_profile_enable(m, 0) stops recording. */
+   fr_profile_enable(m, k) with k >= 1 (re)starts the counters and times every k-th stage (one
+   event pair around its interface kernel and one around its element kernel; each recorded event
+   costs the stream a few microseconds, so k > 1 samples with less overhead);
+   fr_profile_enable(m, 0) stops recording. */
 typedef struct {
   int64_t stage_launches, face_launches;
   double stage_ms, face_ms;   /* summed device time of those launches                     */

@@ -41,6 +41,8 @@ struct fr_mesh {
     int64_t points;
   };
   bool prof = false;
+  int prof_stride = 1;     // time every prof_stride-th stage (interface + element kernel)
+  int64_t prof_count = 0;
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<Rec> recs;
@@ -201,14 +203,15 @@ FaceArgs face_args(fr_mesh* m) {
 int stage(fr_mesh* m, const double* us, const double* un, double* out, double a, double b, double c,
           bool traces) {
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-  if (m->prof) {
+  const bool rec = m->prof && (m->prof_count++ % m->prof_stride) == 0;
+  if (rec) {
     e0 = m->next_event();
     e1 = m->next_event();
     e2 = m->next_event();
     cudaEventRecord(e0, m->stream);
   }
   FR_TRY(launch_faces(m->cfg.precision, m->dim, m->p, face_args(m), m->ops, m->stream, &m->err));
-  if (m->prof) {
+  if (rec) {
     cudaEventRecord(e1, m->stream);
     int64_t nsub = int64_t(1) << (m->dim - 1);
     m->recs.push_back({0, e0, e1, (m->n_conf + m->n_hang * nsub) * m->Nf});
@@ -228,7 +231,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.b = b;
   S.c = c;
   FR_TRY(launch_stage(m->cfg.precision, m->dim, m->p, S, m->ops, m->stream, &m->err));
-  if (m->prof) {
+  if (rec) {
     cudaEventRecord(e2, m->stream);
     m->recs.push_back({1, e1, e2, m->M * m->N});
   }
@@ -697,6 +700,8 @@ int fr_profile_enable(fr_mesh* m, int on) {
   if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
   FR_CUDA(&m->err, cudaStreamSynchronize(m->stream));
   m->prof = on != 0;
+  m->prof_stride = on > 1 ? on : 1;
+  m->prof_count = 0;
   m->recs.clear();
   m->ev_used = 0;
   m->launches0 = launch_counter();

@@ -165,19 +165,28 @@ __global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid
 // on every mortar piece, then the coarse side's L2 back-projection, owner-computes, Sec. 4.3), the
 // others conforming faces (one thread per face point).  The heavier hanging blocks come first so
 // that they are not left running alone at the end of the grid.
+// block size of the interface kernel: 64 threads (more, smaller blocks spread one partial wave
+// evenly over the SMs) unless one hanging face needs more threads than that
+template <int DIM, int NP>
+struct FaceCfg {
+  static constexpr int PER = (1 << (DIM - 1)) * (DIM == 2 ? NP : NP * NP);
+  static constexpr int T = PER > 64 ? 128 : 64;
+  static constexpr int FPB = T / PER;
+};
+
 template <int DIM, int NP, class T>
-__global__ void __launch_bounds__(128) k_faces_t(FaceArgs A, const __grid_constant__ OpsT<T> ops) {
+__global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, const __grid_constant__ OpsT<T> ops) {
   using S = Sz<DIM, NP>;
   constexpr int NV = S::NV, NF = S::NF, NFC = S::NFC, NSUB = S::NSUB;
-  constexpr int PER = NSUB * NF;
-  constexpr int FPB = (128 / PER) > 0 ? 128 / PER : 1;
+  constexpr int PER = FaceCfg<DIM, NP>::PER, BT = FaceCfg<DIM, NP>::T;
+  constexpr int FPB = FaceCfg<DIM, NP>::FPB;
   __shared__ T sF[FPB][NSUB][NV][NF];
   const T* trace = static_cast<const T*>(A.trace);
   T* fcomm = static_cast<T*>(A.fcomm);
   const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
   const int tid = threadIdx.x;
   if (int64_t(blockIdx.x) >= A.nb_hang) {
-    int64_t idx = (int64_t(blockIdx.x) - A.nb_hang) * 128 + tid;
+    int64_t idx = (int64_t(blockIdx.x) - A.nb_hang) * BT + tid;
     int64_t face = idx / NF;
     int q = int(idx % NF);
     if (face >= A.n_conf) return;
@@ -448,14 +457,15 @@ int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps&
 
 template <class T>
 int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t s, Err* err) {
-  int NF = ipow_k(p + 1, dim - 1), PER = (1 << (dim - 1)) * NF;
-  int FPB = 128 / PER > 0 ? 128 / PER : 1;
-  A.nb_conf = (A.n_conf * NF + 127) / 128;
-  A.nb_hang = (A.n_hang + FPB - 1) / FPB;
-  int64_t nb = A.nb_conf + A.nb_hang;
-  if (nb == 0) return 0;
+  if (A.n_conf + A.n_hang == 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
-  FR_NP_DISPATCH(dim, p, (k_faces_t<DD, NN, T><<<unsigned(nb), 128, 0, s>>>(A, ops)));
+  FR_NP_DISPATCH(dim, p, ({
+                   using FC = FaceCfg<DD, NN>;
+                   const int NF = DD == 2 ? NN : NN * NN;
+                   A.nb_conf = (A.n_conf * NF + FC::T - 1) / FC::T;
+                   A.nb_hang = (A.n_hang + FC::FPB - 1) / FC::FPB;
+                   k_faces_t<DD, NN, T><<<unsigned(A.nb_conf + A.nb_hang), FC::T, 0, s>>>(A, ops);
+                 }));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -319,8 +319,9 @@ class Mesh:
     def set_time(self, t):
         self._ck(load().fr_set_time(self.h, C.c_double(t)))
 
-    def profile_enable(self, on=True):
-        self._ck(load().fr_profile_enable(self.h, 1 if on else 0))
+    def profile_enable(self, on=True, stride=1):
+        """Per-kernel event timing of every `stride`-th stage (0/False stops)."""
+        self._ck(load().fr_profile_enable(self.h, max(1, int(stride)) if on else 0))
 
     def profile_read(self):
         o = FRProfile()
