@@ -1,0 +1,113 @@
+"""More GPU parity cases against the oracle: 3D runs with adaptation, checkpoint/restart, the
+paper's analytic-centre indicator, degenerate flags, uniform meshes, extreme degrees."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2306_06744_gb300 import fr
+from paper_2306_06744_gb300 import workloads as W
+from tests.test_gpu_fr import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _cfg(name, **kw):
+    c = W.config(name)
+    c.update(kw)
+    return c
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_3d_steps_with_adaptation(prec):
+    cfg = _cfg("vortex3d_p2_tube", Dbase=2, Dmax=4, th_refine=0.02, th_coarsen=0.005)
+    g = fr.Mesh(dict(cfg, precision=prec))
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    for cycle in range(3):
+        g.step(10)
+        o.step(10)
+        assert rel_l2(g.state(), o.state()) < 1e-10
+        fo, _ = o.flags()
+        g.adapt(fo)
+        o.adapt(fo)
+        assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-10
+
+
+def test_checkpoint_restart_is_bit_exact():
+    cfg = _cfg("vortex2d_p2_small")
+    a = fr.Mesh(cfg)
+    a.step(10)
+    a.adapt()
+    a.step(5)
+    keys, u, t = a.leaves(), a.state(), a.info()["t"]
+    a.step(7)
+    a.adapt()
+    a.step(3)
+    b = fr.Mesh(cfg)
+    b.set_state(keys, u)
+    b.set_time(t)
+    b.step(7)
+    b.adapt()
+    b.step(3)
+    assert np.array_equal(a.leaves(), b.leaves())
+    assert np.array_equal(a.state(), b.state())
+
+
+def test_analytic_centre_indicator():
+    # Sec. 5.2 criterion: compare the counts of points inside radius 5 and outside radius 6
+    cfg = _cfg("vortex2d_p2_small", L=20.0, Dbase=3, Dmax=5, indicator=1, th_refine=5.0,
+               th_coarsen=6.0, vort=np.array([[10.0, 10.0, 5.0, 1.0]]))
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    g.step(10)
+    o.step(10)
+    fg, eg = g.flags()
+    fo, eo = o.flags()
+    assert np.array_equal(eg, eo)  # integer counts (in - out)
+    assert np.array_equal(fg, fo)
+    g.adapt()
+    o.adapt()
+    assert np.array_equal(g.leaves(), o.leaves())
+
+
+@pytest.mark.parametrize("value", [1, -1, 0])
+def test_uniform_flags(value):
+    cfg = _cfg("vortex2d_p2_small", init_passes=1)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    flags = np.full(g.M, value, dtype=np.int8)
+    g.adapt(flags)
+    o.adapt(flags)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    if value == 0:
+        assert len(g.leaves()) == len(flags)
+
+
+def test_uniform_mesh_without_adaptation():
+    cfg = _cfg("vortex2d_p2_small", Dbase=5, Dmax=5)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert g.M == 1024 and np.array_equal(g.leaves(), o.leaves())
+    g.run(20)
+    o.run(20)
+    assert g.M == 1024 and np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-11
+
+
+@pytest.mark.parametrize("p", [1, 4])
+def test_extreme_degrees(p):
+    cfg = _cfg("vortex2d_p2_small", p=p, Dbase=3, Dmax=5)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    for _ in range(2):
+        g.step(10)
+        o.step(10)
+        fo, _ = o.flags()
+        g.adapt(fo)
+        o.adapt(fo)
+        assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-10
