@@ -162,6 +162,40 @@ __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* 
   if (i < n) out[i] += offs[i / SCAN_TILE];
 }
 
+// second pass for up to SCAN_PREFIX_MAX tiles: every 256-element block lies inside one tile and
+// sums the totals of the tiles before it itself (no third launch); block 0 also writes the total
+constexpr int64_t SCAN_PREFIX_MAX = 256;
+__global__ void __launch_bounds__(256) k_scan_add_prefix(int64_t* __restrict__ out, int64_t n,
+                                                         const int64_t* __restrict__ sums, int64_t nb,
+                                                         int64_t* __restrict__ total) {
+  __shared__ int64_t red[256];
+  const int t = threadIdx.x;
+  const int64_t i0 = int64_t(blockIdx.x) * 256;
+  const int64_t tile = i0 / SCAN_TILE;
+  int64_t a = 0;
+  for (int64_t k = t; k < tile; k += 256) a += sums[k];
+  red[t] = a;
+  __syncthreads();
+  for (int st = 128; st > 0; st >>= 1) {
+    if (t < st) red[t] += red[t + st];
+    __syncthreads();
+  }
+  const int64_t prefix = red[0];
+  if (i0 + t < n) out[i0 + t] += prefix;
+  if (blockIdx.x == 0) {
+    __syncthreads();
+    a = 0;
+    for (int64_t k = t; k < nb; k += 256) a += sums[k];
+    red[t] = a;
+    __syncthreads();
+    for (int st = 128; st > 0; st >>= 1) {
+      if (t < st) red[t] += red[t + st];
+      __syncthreads();
+    }
+    if (t == 0) *total = red[0];
+  }
+}
+
 template <class TIn>
 static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
                      cudaStream_t s, Err* err) {
@@ -172,6 +206,15 @@ static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_tota
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
     k_scan_tile<TIn><<<1, SCAN_T, 0, s>>>(d_in, d_out, n, d_total);
+    FR_LAUNCH_CHECK(err);
+    return 0;
+  }
+  if (nb <= SCAN_PREFIX_MAX) {
+    int64_t* sums1 = S.get<int64_t>(nb);
+    if (!sums1) return set_error(err, FR_ENOMEM, "scan scratch");
+    k_scan_tile<TIn><<<unsigned(nb), SCAN_T, 0, s>>>(d_in, d_out, n, sums1);
+    FR_LAUNCH_CHECK(err);
+    k_scan_add_prefix<<<unsigned((n + 255) / 256), 256, 0, s>>>(d_out, n, sums1, nb, d_total);
     FR_LAUNCH_CHECK(err);
     return 0;
   }

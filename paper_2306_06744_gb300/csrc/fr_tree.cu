@@ -141,33 +141,42 @@ __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_
   return *dA < D - 1;
 }
 
+// one thread per leaf: the leaf's requests over its 3^dim-1 neighbour boxes are counted and then
+// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs
 template <int DIM>
 __global__ void k_bal_count(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
                             int32_t* __restrict__ cnt) {
   constexpr int NO = Nofs<DIM>::value;
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n * NO) return;
-  uint32_t N[3];
-  int dA;
-  bool need = bal_query<DIM>(k, n, g, D, t / NO, int(t % NO), N, &dA);
-  cnt[t] = need ? (D - 1 - dA) << DIM : 0;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int32_t c = 0;
+  if (g.depth(k[i]) == D) {
+    for (int o = 0; o < NO; ++o) {
+      uint32_t N[3];
+      int dA;
+      if (bal_query<DIM>(k, n, g, D, i, o, N, &dA)) c += (D - 1 - dA) << DIM;
+    }
+  }
+  cnt[i] = c;
 }
 
 template <int DIM>
 __global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
                           const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
   constexpr int NO = Nofs<DIM>::value;
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n * NO) return;
-  uint32_t N[3];
-  int dA;
-  if (!bal_query<DIM>(k, n, g, D, t / NO, int(t % NO), N, &dA)) return;
-  int64_t o = offs[t];
-  uint64_t rawN = interleave<DIM>(N);
-  for (int l = dA + 1; l <= D - 1; ++l) {
-    uint64_t span = vol_raw<DIM>(g, l - 1);
-    uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
-    for (int c = 0; c < (1 << DIM); ++c) out[o++] = child_key<DIM>(g, anc, c);
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n || g.depth(k[i]) != D) return;
+  int64_t o = offs[i];
+  for (int oo = 0; oo < NO; ++oo) {
+    uint32_t N[3];
+    int dA;
+    if (!bal_query<DIM>(k, n, g, D, i, oo, N, &dA)) continue;
+    uint64_t rawN = interleave<DIM>(N);
+    for (int l = dA + 1; l <= D - 1; ++l) {
+      uint64_t span = vol_raw<DIM>(g, l - 1);
+      uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
+      for (int c = 0; c < (1 << DIM); ++c) out[o++] = child_key<DIM>(g, anc, c);
+    }
   }
 }
 
@@ -542,24 +551,23 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
 
 int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n_io, int* passes,
                  Alloc& A, cudaStream_t s, Err* err) {
-  const int NO = dim == 2 ? 8 : 26;
   if (passes) *passes = 0;
   Buf<uint64_t> gen, tmp, lin, out;
   int rc = 0;
   for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
     int64_t n = *n_io;
     Scratch S(&A);
-    int32_t* cnt = S.get<int32_t>(n * NO);
-    int64_t* offs = S.get<int64_t>(n * NO);
+    int32_t* cnt = S.get<int32_t>(n);
+    int64_t* offs = S.get<int64_t>(n);
     int64_t* tot = S.get<int64_t>(1);
     if (!cnt || !offs || !tot) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n * NO), TB, 0, s>>>(keys.p, n, g, D, cnt)));
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    if ((rc = scan_counts(cnt, offs, n * NO, tot, S, s, err))) break;
+    if ((rc = scan_counts(cnt, offs, n, tot, S, s, err))) break;
     int64_t G = 0;
     if ((rc = read_i64(tot, &G, s, err))) break;
     if (G == 0) continue;
@@ -567,7 +575,7 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n
     if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G))) ||
         (rc = lin.ensure(A, size_t(G))))
       break;
-    DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n * NO), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
+    DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_gen") : 0)) break;
     if (G <= SMALL_SORT_MAX) {
