@@ -307,18 +307,22 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     fl = m->flags.p;
   }
   Buf<uint64_t> nk;
-  int64_t M1 = 0, nref = 0, ncoarse = 0;
   int passes = 0;
-  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, m->M, nk, &M1, &nref, &ncoarse, m->A, s, err);
-  if (!rc) rc = tree_balance(m->dim, m->g, m->cfg.Dbase + 2, nk, &M1, &passes, m->A, s, err);
+  Scratch Sc(&m->A);
+  int64_t* ctl = Sc.get<int64_t>(4);
+  int64_t h_ctl[4] = {0, 0, 0, 0};
+  int rc = ctl ? 0 : set_error(err, FR_ENOMEM, "adapt scratch");
+  if (!rc) rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, m->M, nk, ctl, m->A, s, err);
+  if (!rc)
+    rc = tree_balance(m->dim, m->g, m->cfg.Dbase + 2, nk, ctl, m->M << m->dim, h_ctl, &passes, m->A, s, err);
   if (rc) {
     nk.release(m->A);
     return rc;
   }
+  const int64_t M1 = h_ctl[0], nref = h_ctl[2], ncoarse = h_ctl[3];
   Buf<double> nu;
   Buf<int32_t> src;
   Buf<int8_t> tag;
-  Scratch Sc(&m->A);
   const int32_t* map_bad = nullptr;
   if (transfer) {
     int32_t* bad = Sc.get<int32_t>(1);
@@ -861,14 +865,21 @@ static int balance_or_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys
   FR_TRY(tree_validate(dim, g, d_keys, n, 0, Dmax, &ok, A, s, err));
   if (!ok) return set_error(err, FR_EINVAL, "input is not a complete sorted linear tree");
   Buf<uint64_t> k;
-  int64_t m = n;
+  Scratch S(&A);
+  int64_t* ctl = S.get<int64_t>(4);
+  if (!ctl) return set_error(err, FR_ENOMEM, "scratch");
+  int64_t h_ctl[4] = {n, 0, 0, 0};
+  int64_t n_ub = n;
   if (d_flags) {
-    rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, &m, nullptr, nullptr, A, s, err);
+    rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, ctl, A, s, err);
+    n_ub = n << dim;
   } else {
     rc = k.ensure(A, n);
     if (!rc) rc = cudaMemcpyAsync(k.p, d_keys, size_t(n) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
+    if (!rc) rc = cudaMemcpyAsync(ctl, h_ctl, sizeof(int64_t), cudaMemcpyHostToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
   }
-  if (!rc) rc = tree_balance(dim, g, d_flags ? Dbase + 2 : 2, k, &m, nullptr, A, s, err);
+  if (!rc) rc = tree_balance(dim, g, d_flags ? Dbase + 2 : 2, k, ctl, n_ub, h_ctl, nullptr, A, s, err);
+  const int64_t m = h_ctl[0];
   *n_out = m;
   if (!rc && m > cap) rc = set_error(err, FR_EOVERFLOW, "output capacity too small");
   if (!rc) rc = cudaMemcpyAsync(d_out, k.p, size_t(m) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");

@@ -265,12 +265,16 @@ int tree_complete(int dim, const KG& g, int Dmin, double L, const double* d_pts,
                   Buf<uint64_t>& out, int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
 int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf<uint64_t>& out,
                    int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
+// Control block of an adaptation, on the device: d_ctl[0] leaf count of the tree being built,
+// [1] generated octants of the current balance pass, [2] refined leaves, [3] coarsened groups.
+// The edit leaves its leaf count and statistics there without a host synchronisation; its
+// output holds at most n << dim leaves.
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
-              int64_t n, Buf<uint64_t>& out, int64_t* n_out, int64_t* n_ref, int64_t* n_coarse,
-              Alloc& A, cudaStream_t s, Err* err);
-// balances `keys` (n leaves) in place for depth passes D = Dmax .. Dlow
-int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n, int* passes,
-                 Alloc& A, cudaStream_t s, Err* err);
+              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, Alloc& A, cudaStream_t s, Err* err);
+// balances `keys` in place for depth passes D = Dmax .. Dlow; the leaf count is d_ctl[0] on
+// entry (at most n_ub), and on return h_ctl holds the final control block (h_ctl[0] = leaves)
+int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl, int64_t n_ub,
+                 int64_t h_ctl[4], int* passes, Alloc& A, cudaStream_t s, Err* err);
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
              int64_t n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad, cudaStream_t s, Err* err);
 // connectivity; d_contrib (may be null) receives [n][2dim][4] coarse-side contributors

@@ -48,6 +48,13 @@ static void raw_put(const fr_allocator* user, cudaStream_t stream, void* p) {
 void* Alloc::get(size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) / 256 * 256;
+  if (bytes > 65536) {
+    // eight size classes per power of two (at most 12.5% slack): a request that grows by a few
+    // leaves from one adaptation to the next then finds last time's block in the cache
+    int lg = 63 - __builtin_clzll(bytes);
+    size_t step = size_t(1) << (lg - 3);
+    bytes = (bytes + step - 1) / step * step;
+  }
   if (cache) {
     // smallest cached block that fits without wasting more than half of it
     size_t best = size_t(-1);

@@ -142,15 +142,18 @@ __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_
 }
 
 // one thread per leaf: the leaf's requests over its 3^dim-1 neighbour boxes are counted and then
-// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs
+// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs.  The
+// leaf count is read on the device (threads up to an upper bound write zeros past it), so the
+// pass needs no host synchronisation before it starts.
 template <int DIM>
-__global__ void k_bal_count(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
-                            int32_t* __restrict__ cnt) {
+__global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __restrict__ d_n,
+                            int64_t n_ub, KG g, int D, int32_t* __restrict__ cnt) {
   constexpr int NO = Nofs<DIM>::value;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n_ub) return;
+  const int64_t n = *d_n;
   int32_t c = 0;
-  if (g.depth(k[i]) == D) {
+  if (i < n && g.depth(k[i]) == D) {
     for (int o = 0; o < NO; ++o) {
       uint32_t N[3];
       int dA;
@@ -208,34 +211,49 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys
   for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = sk[i];
 }
 
-// replace every leaf by the linearised generated octants inside it (or keep it)
+// Merge of the sorted generated octants S (duplicates and ancestors still present) into the tree.
+// Every generated octant lies strictly inside one current leaf, and the octants inside a leaf
+// cover it once linearised (path splitting emits all 2^dim children at each level), so a leaf
+// with a non-empty range [lo, hi) is replaced by the linearised octants of that range and any
+// other leaf is kept.  Linearisation keeps S[r] unless S[r+1] equals it or lies inside it.
+template <int DIM>
+__device__ __forceinline__ bool lin_keep(const uint64_t* __restrict__ S, int64_t nS, const KG& g, int64_t r) {
+  if (r + 1 >= nS) return true;
+  uint64_t a = S[r], b = S[r + 1];
+  return !(a == b || is_ancestor<DIM>(g, a, b));
+}
 template <int DIM>
 __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t n,
-                              const uint64_t* __restrict__ S, const int64_t* __restrict__ d_nS, KG g,
+                              const uint64_t* __restrict__ S, int64_t nS, KG g,
                               int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t nS = *d_nS;
   uint64_t key = k[i];
   int64_t lo = lower_bound_dev(S, nS, key);
   int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
-  cnt[i] = hi > lo ? int32_t(hi - lo) : 1;
+  int32_t c = 1;
+  if (hi > lo) {
+    c = 0;
+    for (int64_t r = lo; r < hi; ++r) c += lin_keep<DIM>(S, nS, g, r);
+  }
+  cnt[i] = c;
   lo_out[i] = hi > lo ? lo : -1;  // -1: the leaf is kept as it is
 }
-
+template <int DIM>
 __global__ void k_merge_write(const uint64_t* __restrict__ k, int64_t n,
-                              const uint64_t* __restrict__ S, const int32_t* __restrict__ cnt,
-                              const int64_t* __restrict__ lo, const int64_t* __restrict__ offs,
-                              uint64_t* __restrict__ out) {
+                              const uint64_t* __restrict__ S, int64_t nS, KG g,
+                              const int32_t* __restrict__ cnt, const int64_t* __restrict__ lo,
+                              const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int64_t o = offs[i], l = lo[i];
   if (l < 0) {
     out[o] = k[i];
-  } else {
-    int c = cnt[i];
-    for (int r = 0; r < c; ++r) out[o + r] = S[l + r];
+    return;
   }
+  const int64_t end = o + cnt[i];
+  for (int64_t r = l; o < end; ++r)
+    if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
 }
 
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
@@ -522,58 +540,67 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys, int64_t n, Buf<uint64
 }
 
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
-              int64_t n, Buf<uint64_t>& out, int64_t* n_out, int64_t* n_ref, int64_t* n_coarse,
-              Alloc& A, cudaStream_t s, Err* err) {
+              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, Alloc& A, cudaStream_t s, Err* err) {
   Scratch S(&A);
   int8_t* act = S.get<int8_t>(n);
   int32_t* cnt = S.get<int32_t>(n);
   int64_t* offs = S.get<int64_t>(n);
-  int64_t* res = S.get<int64_t>(3);  // [0] refined, [1] coarsened groups, [2] new leaf count
-  if (!act || !cnt || !offs || !res) return set_error(err, FR_ENOMEM, "edit scratch");
-  // the edited tree has at most 2^dim leaves per old leaf: size the output for that bound so
-  // that the count, the scan and the write need a single host synchronisation at the end
+  if (!act || !cnt || !offs) return set_error(err, FR_ENOMEM, "edit scratch");
+  // the edited tree has at most 2^dim leaves per old leaf: the output is sized for that bound and
+  // the leaf count stays on the device (d_ctl[0]) for the balance passes
   FR_TRY(out.ensure(A, size_t(n) << dim));
-  FR_CUDA(err, cudaMemsetAsync(res, 0, 16, s));
+  FR_CUDA(err, cudaMemsetAsync(d_ctl + 2, 0, 16, s));
   DIM_DISPATCH(dim, (k_edit_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, d_flags, n, g, Dbase, act, cnt)));
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts(cnt, offs, n, res + 2, S, s, err));
+  FR_TRY(scan_counts(cnt, offs, n, d_ctl, S, s, err));
   DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p,
-                                                               reinterpret_cast<unsigned long long*>(res))));
+                                                               reinterpret_cast<unsigned long long*>(d_ctl + 2))));
   FR_LAUNCH_CHECK(err);
-  int64_t h[3] = {0, 0, 0};
-  FR_CUDA(err, cudaMemcpyAsync(h, res, 24, cudaMemcpyDeviceToHost, s));
-  FR_CUDA(err, cudaStreamSynchronize(s));
-  *n_out = h[2];
-  if (n_ref) *n_ref = h[0];
-  if (n_coarse) *n_coarse = h[1];
   return 0;
 }
 
-int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n_io, int* passes,
-                 Alloc& A, cudaStream_t s, Err* err) {
+// above this bound on the leaf count a pass first reads the exact count from the device
+constexpr int64_t BAL_UB_MAX = int64_t(1) << 19;
+
+int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl, int64_t n_ub,
+                 int64_t h_ctl[4], int* passes, Alloc& A, cudaStream_t s, Err* err) {
   if (passes) *passes = 0;
-  Buf<uint64_t> gen, tmp, lin, out;
+  Buf<uint64_t> gen, tmp, out;
   int rc = 0;
+  bool known = false;  // h_ctl[0] holds the current leaf count
   for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
-    int64_t n = *n_io;
+    if (!known && n_ub > BAL_UB_MAX) {
+      // large trees: counting and scanning up to a loose bound costs more than a synchronisation
+      if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = set_error(err, FR_ECUDA, "balance count read");
+        break;
+      }
+      n_ub = h_ctl[0];
+    }
     Scratch S(&A);
-    int32_t* cnt = S.get<int32_t>(n);
-    int64_t* offs = S.get<int64_t>(n);
-    int64_t* tot = S.get<int64_t>(1);
-    if (!cnt || !offs || !tot) {
+    int32_t* cnt = S.get<int32_t>(n_ub);
+    int64_t* offs = S.get<int64_t>(n_ub);
+    if (!cnt || !offs) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, g, D, cnt)));
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    if ((rc = scan_counts(cnt, offs, n, tot, S, s, err))) break;
-    int64_t G = 0;
-    if ((rc = read_i64(tot, &G, s, err))) break;
+    if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + 1, S, s, err))) break;
+    // the pass's one synchronisation: leaf count, generated count (and the edit's statistics)
+    if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = set_error(err, FR_ECUDA, "balance count read");
+      break;
+    }
+    known = true;
+    const int64_t n = h_ctl[0], G = h_ctl[1];
+    n_ub = n;
     if (G == 0) continue;
     if (passes) ++*passes;
-    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G))) ||
-        (rc = lin.ensure(A, size_t(G))))
+    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G))) || (rc = out.ensure(A, size_t(n + G))))
       break;
     DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
     ++launch_counter();
@@ -585,19 +612,6 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n
     } else if ((rc = radix_sort_keys(gen.p, tmp.p, G, dim * g.Dmax + g.mb, S, s, err))) {
       break;
     }
-    // linearise the generated octants (sorted): the count stays on the device
-    int32_t* cl = S.get<int32_t>(G);
-    int64_t* ol = S.get<int64_t>(G);
-    int64_t* nS = S.get<int64_t>(1);
-    if (!cl || !ol || !nS) {
-      rc = set_error(err, FR_ENOMEM, "balance linearise scratch");
-      break;
-    }
-    DIM_DISPATCH(dim, (k_lin_count<D_><<<nblk(G), TB, 0, s>>>(gen.p, G, g, cl)));
-    ++launch_counter();
-    if ((rc = scan_counts(cl, ol, G, nS, S, s, err))) break;
-    k_compact<<<nblk(G), TB, 0, s>>>(gen.p, cl, ol, G, lin.p);
-    ++launch_counter();
     int32_t* cnt2 = S.get<int32_t>(n);
     int64_t* lo = S.get<int64_t>(n);
     int64_t* offs2 = S.get<int64_t>(n);
@@ -605,25 +619,27 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* n
       rc = set_error(err, FR_ENOMEM, "balance merge scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, lin.p, nS, g, cnt2, lo)));
+    DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, gen.p, G, g, cnt2, lo)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_count") : 0)) break;
-    if ((rc = scan_counts(cnt2, offs2, n, tot, S, s, err))) break;
-    int64_t Mn = 0;
-    if ((rc = read_i64(tot, &Mn, s, err))) break;
-    if ((rc = out.ensure(A, size_t(Mn)))) break;
-    k_merge_write<<<nblk(n), TB, 0, s>>>(keys.p, n, lin.p, cnt2, lo, offs2, out.p);
+    // the merged tree has at most n + G leaves; its count goes to d_ctl[0] on the device
+    if ((rc = scan_counts(cnt2, offs2, n, d_ctl, S, s, err))) break;
+    DIM_DISPATCH(dim, (k_merge_write<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, gen.p, G, g, cnt2, lo, offs2, out.p)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_write") : 0)) break;
-    // out becomes the tree
-    Buf<uint64_t> t = keys;
+    Buf<uint64_t> t = keys;  // the merged tree becomes the tree
     keys = out;
     out = t;
-    *n_io = Mn;
+    n_ub = n + G;
+    known = false;
+  }
+  if (!rc && !known) {
+    if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = set_error(err, FR_ECUDA, "balance count read");
   }
   gen.release(A);
   tmp.release(A);
-  lin.release(A);
   out.release(A);
   return rc;
 }
