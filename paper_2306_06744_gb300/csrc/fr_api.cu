@@ -65,9 +65,14 @@ inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); 
 // faces per element: conforming faces owned by their minus side (checked on the plus face of
 // each element), coarse sides of hanging faces
 template <int DIM>
-__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int64_t* __restrict__ c) {
+__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M_ub, const int64_t* __restrict__ d_M,
+                             int64_t* __restrict__ c) {
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= M) return;
+  if (e >= M_ub) return;
+  if (d_M && e >= *d_M) {
+    c[e] = 0;
+    return;
+  }
   int a = 0, b = 0;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) {
@@ -80,10 +85,10 @@ __global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M, int64_
 
 template <int DIM>
 __global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
-                             int64_t M, const int64_t* __restrict__ off, int32_t* __restrict__ conf,
-                             int32_t* __restrict__ hang, int32_t* __restrict__ hcon) {
+                             int64_t M_ub, const int64_t* __restrict__ d_M, const int64_t* __restrict__ off,
+                             int32_t* __restrict__ conf, int32_t* __restrict__ hang, int32_t* __restrict__ hcon) {
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= M) return;
+  if (e >= M_ub || (d_M && e >= *d_M)) return;
   int64_t a = off[e] & 0xFFFFFFFFll, b = off[e] >> 32;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) {
@@ -118,59 +123,79 @@ int check_cfg(const fr_config* c, Err* err) {
   return 0;
 }
 
-// connectivity and face lists of the current tree; `extra_bad` (device flag, may be null) is read
-// in the same host synchronisation
-int rebuild_conn(fr_mesh* m, const int32_t* extra_bad = nullptr) {
+// Issues the connectivity and face lists of `keys` into the mesh's tables: the leaf count is
+// *d_n on the device (at most n_ub) or exactly n_ub (d_n null).  The packed face-list counts go
+// to *d_faces and a 2:1 violation to bad[0]; `hcon` receives the per-hanging-face contributors.
+static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int64_t* d_n, int64_t* d_faces,
+                      int32_t* bad, Buf<int32_t>& hcon) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
-  int64_t M = m->M, S = M * m->nfc;
+  const int64_t S = n_ub * m->nfc;
   FR_TRY(m->nbr.ensure(m->A, S));
   FR_TRY(m->ftype.ensure(m->A, S));
   FR_TRY(m->slot.ensure(m->A, S));
   FR_TRY(m->contrib.ensure(m->A, S * 4));
   Scratch Sc(&m->A);
-  int32_t* bad = Sc.get<int32_t>(2);
-  int64_t* cnt = Sc.get<int64_t>(M);
-  int64_t* off = Sc.get<int64_t>(M);
-  int64_t* tot = Sc.get<int64_t>(1);
-  if (!bad || !cnt || !off || !tot) return set_error(err, FR_ENOMEM, "conn scratch");
-  FR_CUDA(err, cudaMemsetAsync(bad, 0, 8, s));
+  int64_t* cnt = Sc.get<int64_t>(n_ub);
+  int64_t* off = Sc.get<int64_t>(n_ub);
+  if (!cnt || !off) return set_error(err, FR_ENOMEM, "conn scratch");
   FR_CUDA(err, cudaMemsetAsync(m->contrib.p, 0xff, size_t(S) * 16, s));
-  if (extra_bad) FR_CUDA(err, cudaMemcpyAsync(bad + 1, extra_bad, 4, cudaMemcpyDeviceToDevice, s));
-  FR_TRY(tree_conn(m->dim, m->g, m->keys.p, M, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
+  FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
   if (m->dim == 2)
-    k_face_count<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cnt);
+    k_face_count<2><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, n_ub, d_n, cnt);
   else
-    k_face_count<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, M, cnt);
+    k_face_count<3><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, n_ub, d_n, cnt);
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts64(cnt, off, M, tot, Sc, s, err));
+  FR_TRY(scan_counts64(cnt, off, n_ub, d_faces, Sc, s, err));
   // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
-  // bound so the writes need no further synchronisation
-  FR_TRY(m->conf.ensure(m->A, size_t(M) * m->dim));
-  FR_TRY(m->hang.ensure(m->A, size_t(M) * m->nfc));
-  Buf<int32_t> hcon;
-  FR_TRY(hcon.ensure(m->A, size_t(M) * m->nfc * 4));
+  // bound so the writes need no synchronisation
+  FR_TRY(m->conf.ensure(m->A, size_t(n_ub) * m->dim));
+  FR_TRY(m->hang.ensure(m->A, size_t(n_ub) * m->nfc));
+  FR_TRY(hcon.ensure(m->A, size_t(n_ub) * m->nfc * 4));
   if (m->dim == 2)
-    k_face_write<2><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, off, m->conf.p, m->hang.p, hcon.p);
+    k_face_write<2><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, m->contrib.p, n_ub, d_n, off, m->conf.p, m->hang.p, hcon.p);
   else
-    k_face_write<3><<<nblk(M), TB, 0, s>>>(m->ftype.p, m->contrib.p, M, off, m->conf.p, m->hang.p, hcon.p);
+    k_face_write<3><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, m->contrib.p, n_ub, d_n, off, m->conf.p, m->hang.p, hcon.p);
   FR_LAUNCH_CHECK(err);
-  int64_t h = 0;
-  int32_t hb[2] = {0, 0};
-  FR_CUDA(err, cudaMemcpyAsync(&h, tot, 8, cudaMemcpyDeviceToHost, s));
-  FR_CUDA(err, cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s));
-  FR_CUDA(err, cudaStreamSynchronize(s));
+  return 0;
+}
+
+// after the synchronisation: checks the flags (bad[0] 2:1 violation, bad[1] mapping), keeps the
+// face-list counts and the per-hanging-face contributor table
+static int conn_finish(fr_mesh* m, int64_t faces, const int32_t* hb, Buf<int32_t>& hcon) {
+  Err* err = &m->err;
   if (hb[0]) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
   if (hb[1])
     return set_error(err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
-  m->n_conf = h & 0xFFFFFFFFll;
-  m->n_hang = h >> 32;
-  // keep the per-hanging-face contributor table in `contrib` (the per element-face table is not
-  // needed after the lists are built)
-  Buf<int32_t> old = m->contrib;
+  m->n_conf = faces & 0xFFFFFFFFll;
+  m->n_hang = faces >> 32;
+  Buf<int32_t> old = m->contrib;  // the per element-face table is not needed after the lists
   m->contrib = hcon;
+  hcon = Buf<int32_t>{};
   old.release(m->A);
   return 0;
+}
+
+// connectivity and face lists of the current tree (one host synchronisation)
+int rebuild_conn(fr_mesh* m) {
+  Err* err = &m->err;
+  cudaStream_t s = m->stream;
+  Scratch Sc(&m->A);
+  int32_t* bad = Sc.get<int32_t>(2);
+  int64_t* tot = Sc.get<int64_t>(1);
+  if (!bad || !tot) return set_error(err, FR_ENOMEM, "conn scratch");
+  FR_CUDA(err, cudaMemsetAsync(bad, 0, 8, s));
+  Buf<int32_t> hcon;
+  int rc = conn_issue(m, m->keys.p, m->M, nullptr, tot, bad, hcon);
+  int64_t h = 0;
+  int32_t hb[2] = {0, 0};
+  if (!rc && (cudaMemcpyAsync(&h, tot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    rc = set_error(err, FR_ECUDA, "conn read");
+  if (!rc) rc = conn_finish(m, h, hb, hcon);
+  hcon.release(m->A);
+  return rc;
 }
 
 int ensure_state(fr_mesh* m, int64_t M) {
@@ -296,6 +321,11 @@ struct Timer {
 };
 
 // Adaptation: edit the tree with the flags, balance, and (if `transfer`) carry the state over.
+// Adaptations of meshes up to this many leaves (times 2^dim, plus the balance passes' octant
+// capacity) are issued without host synchronisations until the connectivity counts are read:
+// below it launch and synchronisation latency, not the kernels, set the cost of an adaptation.
+constexpr int64_t FAST_ADAPT_MAX = int64_t(1) << 20;
+
 int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool transfer) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
@@ -306,47 +336,70 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     FR_TRY(compute_flags(m, nullptr));
     fl = m->flags.p;
   }
-  Buf<uint64_t> nk;
-  int passes = 0;
+  const int Dlow = m->cfg.Dbase + 2;
+  const int64_t M0 = m->M;
+  int64_t n_ub = M0 << m->dim;
+  bool fast = transfer && n_ub + int64_t(m->g.Dmax) * 4096 <= FAST_ADAPT_MAX;
   Scratch Sc(&m->A);
-  int64_t* ctl = Sc.get<int64_t>(4);
-  int64_t h_ctl[4] = {0, 0, 0, 0};
-  int rc = ctl ? 0 : set_error(err, FR_ENOMEM, "adapt scratch");
-  if (!rc) rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, m->M, nk, ctl, m->A, s, err);
-  if (!rc)
-    rc = tree_balance(m->dim, m->g, m->cfg.Dbase + 2, nk, ctl, m->M << m->dim, h_ctl, &passes, m->A, s, err);
-  if (rc) {
-    nk.release(m->A);
-    return rc;
-  }
-  const int64_t M1 = h_ctl[0], nref = h_ctl[2], ncoarse = h_ctl[3];
+  int64_t* ctl = Sc.get<int64_t>(CTL_SLOTS);
+  int32_t* bad = Sc.get<int32_t>(2);
+  if (!ctl || !bad) return set_error(err, FR_ENOMEM, "adapt scratch");
+  int64_t h_ctl[CTL_SLOTS] = {0};
+  int32_t hb[2] = {0, 0};
+  Buf<uint64_t> nk;
   Buf<double> nu;
-  Buf<int32_t> src;
+  Buf<int32_t> src, hcon;
   Buf<int8_t> tag;
-  const int32_t* map_bad = nullptr;
-  if (transfer) {
-    int32_t* bad = Sc.get<int32_t>(1);
-    if (!bad) rc = set_error(err, FR_ENOMEM, "adapt scratch");
-    if (!rc) rc = src.ensure(m->A, M1);
-    if (!rc) rc = tag.ensure(m->A, M1);
-    if (!rc) rc = cudaMemsetAsync(bad, 0, 4, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "memset");
-    if (!rc) rc = tree_map(m->dim, m->g, m->keys.p, m->M, nk.p, M1, src.p, tag.p, bad, s, err);
-    T.mark(1);
-    if (!rc) rc = nu.ensure(m->A, size_t(M1) * m->EU);
-    if (!rc) rc = launch_transfer(m->dim, m->p, m->g, m->keys.p, nk.p, src.p, tag.p, M1, m->ops, m->u.p, nu.p, s, err);
-    map_bad = bad;
-  } else {
-    T.mark(1);
+  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, m->A, s, err);
+  if (!rc) rc = cudaMemsetAsync(bad, 0, 8, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "memset");
+  // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
+  auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
+    int r = 0;
+    if (transfer) {
+      if (!r) r = src.ensure(m->A, nb);
+      if (!r) r = tag.ensure(m->A, nb);
+      if (!r) r = tree_map(m->dim, m->g, m->keys.p, M0, nk.p, nb, d_n, src.p, tag.p, bad + 1, s, err);
+      T.mark(1);
+      if (!r) r = nu.ensure(m->A, size_t(nb) * m->EU);
+      if (!r)
+        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, nk.p, src.p, tag.p, nb, d_n, m->ops, m->u.p, nu.p, s, err);
+    } else {
+      T.mark(1);
+    }
+    T.mark(2);
+    if (!r) r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon);
+    if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess))
+      r = set_error(err, FR_ECUDA, "adapt read");
+    return r;
+  };
+  if (!rc && fast) {
+    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err);
+    if (!rc) rc = rest(n_ub, ctl + CTL_N);
+    if (!rc && h_ctl[CTL_OVER] != 0) {
+      // a balance pass generated more octants than the issued passes hold: finish the balance
+      // from that depth with exact sizes and redo the rest
+      const int Dov = int(h_ctl[CTL_OVER]);
+      if (cudaMemsetAsync(ctl + CTL_OVER, 0, 8, s) != cudaSuccess || cudaMemsetAsync(bad, 0, 8, s) != cudaSuccess)
+        rc = set_error(err, FR_ECUDA, "memset");
+      if (!rc) rc = tree_balance(m->dim, m->g, Dov, Dlow, nk, ctl, n_ub, h_ctl, m->A, s, err);
+      hcon.release(m->A);
+      fast = false;
+    }
+  } else if (!rc) {
+    rc = tree_balance(m->dim, m->g, m->g.Dmax, Dlow, nk, ctl, n_ub, h_ctl, m->A, s, err);
   }
-  T.mark(2);
+  if (!rc && !fast) rc = rest(h_ctl[CTL_N], nullptr);
+  const int64_t M1 = h_ctl[CTL_N];
   src.release(m->A);
   tag.release(m->A);
   if (rc) {
     nk.release(m->A);
     nu.release(m->A);
+    hcon.release(m->A);
     return rc;
   }
-  int64_t M0 = m->M;
   Buf<uint64_t> ok = m->keys;
   m->keys = nk;
   ok.release(m->A);
@@ -356,20 +409,22 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     m->u = nu;
     ou.release(m->A);
   }
+  rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
+  hcon.release(m->A);
+  FR_TRY(rc);
   FR_TRY(m->w.ensure(m->A, size_t(M1) * m->EU));
   FR_TRY(m->trace.ensure(m->A, size_t(M1) * m->EF));
   FR_TRY(m->fcomm.ensure(m->A, size_t(M1) * m->EF));
   FR_TRY(m->flags.ensure(m->A, size_t(M1)));
   if (!transfer) FR_TRY(m->u.ensure(m->A, size_t(M1) * m->EU));
-  FR_TRY(rebuild_conn(m, map_bad));
   if (transfer) FR_TRY(refresh_traces(m));
   T.mark(3);
   if (st) {
     st->M_old = M0;
     st->M_new = M1;
-    st->n_refined = nref;
-    st->n_coarsened = ncoarse;
-    st->balance_passes = passes;
+    st->n_refined = h_ctl[CTL_REF];
+    st->n_coarsened = h_ctl[CTL_COARSE];
+    st->balance_passes = int(h_ctl[CTL_PASSES]);
     st->ms_tree = T.ms(0, 1);
     st->ms_transfer = T.ms(1, 2);
     st->ms_conn = T.ms(2, 3);
@@ -866,9 +921,9 @@ static int balance_or_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys
   if (!ok) return set_error(err, FR_EINVAL, "input is not a complete sorted linear tree");
   Buf<uint64_t> k;
   Scratch S(&A);
-  int64_t* ctl = S.get<int64_t>(4);
+  int64_t* ctl = S.get<int64_t>(CTL_SLOTS);
   if (!ctl) return set_error(err, FR_ENOMEM, "scratch");
-  int64_t h_ctl[4] = {n, 0, 0, 0};
+  int64_t h_ctl[CTL_SLOTS] = {n};
   int64_t n_ub = n;
   if (d_flags) {
     rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, ctl, A, s, err);
@@ -876,10 +931,10 @@ static int balance_or_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys
   } else {
     rc = k.ensure(A, n);
     if (!rc) rc = cudaMemcpyAsync(k.p, d_keys, size_t(n) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
-    if (!rc) rc = cudaMemcpyAsync(ctl, h_ctl, sizeof(int64_t), cudaMemcpyHostToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
+    if (!rc) rc = cudaMemcpyAsync(ctl, h_ctl, sizeof(h_ctl), cudaMemcpyHostToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
   }
-  if (!rc) rc = tree_balance(dim, g, d_flags ? Dbase + 2 : 2, k, ctl, n_ub, h_ctl, nullptr, A, s, err);
-  const int64_t m = h_ctl[0];
+  if (!rc) rc = tree_balance(dim, g, Dmax, d_flags ? Dbase + 2 : 2, k, ctl, n_ub, h_ctl, A, s, err);
+  const int64_t m = h_ctl[CTL_N];
   *n_out = m;
   if (!rc && m > cap) rc = set_error(err, FR_EOVERFLOW, "output capacity too small");
   if (!rc) rc = cudaMemcpyAsync(d_out, k.p, size_t(m) * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "copy");
@@ -937,7 +992,7 @@ int fr_tree_map(int dim, int Dmax, const uint64_t* d_old, int64_t n_old, const u
   int32_t* bad = S.get<int32_t>(1);
   if (!bad) return set_error(err, FR_ENOMEM, "map scratch");
   FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
-  FR_TRY(tree_map(dim, g, d_old, n_old, d_new, n_new, d_src, d_tag, bad, s, err));
+  FR_TRY(tree_map(dim, g, d_old, n_old, d_new, n_new, nullptr, d_src, d_tag, bad, s, err));
   int32_t hb = 0;
   FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
   FR_CUDA(err, cudaStreamSynchronize(s));
@@ -961,7 +1016,7 @@ int fr_tree_conn(int dim, int Dmax, const uint64_t* d_keys, int64_t n, int32_t* 
   int32_t* bad = S.get<int32_t>(1);
   if (!bad) return set_error(err, FR_ENOMEM, "conn scratch");
   FR_CUDA(err, cudaMemsetAsync(bad, 0, 4, s));
-  FR_TRY(tree_conn(dim, g, d_keys, n, d_nbr, d_ftype, d_slot, nullptr, bad, s, err));
+  FR_TRY(tree_conn(dim, g, d_keys, n, nullptr, d_nbr, d_ftype, d_slot, nullptr, bad, s, err));
   int32_t hb = 0;
   FR_CUDA(err, cudaMemcpyAsync(&hb, bad, 4, cudaMemcpyDeviceToHost, s));
   FR_CUDA(err, cudaStreamSynchronize(s));

@@ -265,20 +265,32 @@ int tree_complete(int dim, const KG& g, int Dmin, double L, const double* d_pts,
                   Buf<uint64_t>& out, int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
 int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf<uint64_t>& out,
                    int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
-// Control block of an adaptation, on the device: d_ctl[0] leaf count of the tree being built,
-// [1] generated octants of the current balance pass, [2] refined leaves, [3] coarsened groups.
-// The edit leaves its leaf count and statistics there without a host synchronisation; its
-// output holds at most n << dim leaves.
+// Control block of an adaptation on the device, CTL_SIZE int64 values (layout in fr_tree.cu):
+// [0] leaf count of the tree being built, [1] generated octants of the current balance pass,
+// [2] refined leaves, [3] coarsened groups, [4] overflowed pass depth (0: none), [5] passes that
+// changed the tree, [6] face-list counts (conforming | hanging << 32).
+enum { CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6, CTL_SLOTS = 8 };
+// The edit zeroes the control block and leaves its leaf count and statistics there without a
+// host synchronisation; its output holds at most n << dim leaves.
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
               int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, Alloc& A, cudaStream_t s, Err* err);
-// balances `keys` in place for depth passes D = Dmax .. Dlow; the leaf count is d_ctl[0] on
-// entry (at most n_ub), and on return h_ctl holds the final control block (h_ctl[0] = leaves)
-int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl, int64_t n_ub,
-                 int64_t h_ctl[4], int* passes, Alloc& A, cudaStream_t s, Err* err);
+// balances `keys` in place for depth passes D = Dhigh .. Dlow with exact sizes (one host
+// synchronisation per pass); the leaf count is d_ctl[0] on entry (at most n_ub) and h_ctl
+// (CTL_SLOTS values) holds the final control block on return
+int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
+                 int64_t n_ub, int64_t* h_ctl, Alloc& A, cudaStream_t s, Err* err);
+// the same passes (Dmax .. Dlow) issued without any host synchronisation: each pass may generate
+// at most 4096 octants, *n_ub is raised to a bound of the final leaf count, and a pass that would
+// generate more sets d_ctl[4] to its depth and leaves the tree unchanged from there on (the caller
+// then finishes with tree_balance from that depth)
+int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
+                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err);
+// d_n_new / d_n (nullable): device leaf count of the new tree; n_new / n is then an upper bound
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
-             int64_t n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad, cudaStream_t s, Err* err);
+             int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,
+             cudaStream_t s, Err* err);
 // connectivity; d_contrib (may be null) receives [n][2dim][4] coarse-side contributors
-int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
               Err* err);
 // checks that keys are a complete sorted linear tree with depths in [Dlo, Dhi]

@@ -261,12 +261,12 @@ __global__ void k_indicator(const uint64_t* __restrict__ keys, int64_t M, KG g, 
 template <int DIM, int NP>
 __global__ void k_transfer(KG g, const uint64_t* __restrict__ old_keys,
                            const uint64_t* __restrict__ new_keys, const int32_t* __restrict__ src,
-                           const int8_t* __restrict__ tag, int64_t Mn,
+                           const int8_t* __restrict__ tag, int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
                            const __grid_constant__ DevOps ops, const double* __restrict__ uo,
                            double* __restrict__ un) {
   using S = Sz<DIM, NP>;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= Mn * S::N) return;
+  if (idx >= Mn_ub * S::N || (d_Mn && idx >= *d_Mn * S::N)) return;
   int64_t j = idx / S::N;
   int i = int(idx % S::N);
   int64_t sidx = src[j];
@@ -489,11 +489,11 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
 }
 
 int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
-                    const int32_t* src, const int8_t* tag, int64_t M_new, const DevOps& ops,
-                    const double* u_old, double* u_new, cudaStream_t s, Err* err) {
+                    const int32_t* src, const int8_t* tag, int64_t M_new, const int64_t* d_M_new,
+                    const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err) {
   if (M_new <= 0) return 0;
   int64_t T = M_new * ipow(p + 1, dim);
-  FR_DISPATCH(dim, p, (k_transfer<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(g, old_keys, new_keys, src, tag, M_new, ops, u_old, u_new)));
+  FR_DISPATCH(dim, p, (k_transfer<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(g, old_keys, new_keys, src, tag, M_new, d_M_new, ops, u_old, u_new)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

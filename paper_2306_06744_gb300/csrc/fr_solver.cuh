@@ -53,9 +53,10 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
                      const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
                      const DevOps& ops, const double* u, int8_t* flags, double* eta,
                      cudaStream_t s, Err* err);
+// d_M_new (nullable): device count of new leaves, M_new then an upper bound
 int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
-                    const int32_t* src, const int8_t* tag, int64_t M_new, const DevOps& ops,
-                    const double* u_old, double* u_new, cudaStream_t s, Err* err);
+                    const int32_t* src, const int8_t* tag, int64_t M_new, const int64_t* d_M_new,
+                    const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err);
 // norms: out[0] = sum w|J|(rho_ex-rho)^2, out[1..nv] integrals, out[nv+1] min rho, out[nv+2] min p
 int launch_norms(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
                  const DevProblem& P, const DevOps& ops, const double* u, double* d_partial,

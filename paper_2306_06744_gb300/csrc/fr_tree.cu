@@ -141,19 +141,29 @@ __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_
   return *dA < D - 1;
 }
 
+// The balance kernels read the leaf and octant counts from the adaptation's control block
+// (CTL_* slots), so a whole adaptation can be issued without a host synchronisation; a pass whose
+// octants exceed the capacity it was given is recorded in CTL_OVER, and it and all later passes
+// leave the tree as it is, for the caller to finish with exact sizes.
+
+// generated octants of the current pass that the merge uses: none after an overflow
+__device__ __forceinline__ int64_t bal_nS(const int64_t* ctl, int64_t cap) {
+  const int64_t G = ctl[CTL_G];
+  return (ctl[CTL_OVER] != 0 || G > cap) ? 0 : G;
+}
+
 // one thread per leaf: the leaf's requests over its 3^dim-1 neighbour boxes are counted and then
-// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs.  The
-// leaf count is read on the device (threads up to an upper bound write zeros past it), so the
-// pass needs no host synchronisation before it starts.
+// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs.  Threads
+// up to an upper bound of the leaf count write zeros past it.
 template <int DIM>
-__global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __restrict__ d_n,
+__global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                             int64_t n_ub, KG g, int D, int32_t* __restrict__ cnt) {
   constexpr int NO = Nofs<DIM>::value;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
-  const int64_t n = *d_n;
+  const int64_t n = ctl[CTL_N];
   int32_t c = 0;
-  if (i < n && g.depth(k[i]) == D) {
+  if (i < n && ctl[CTL_OVER] == 0 && g.depth(k[i]) == D) {
     for (int o = 0; o < NO; ++o) {
       uint32_t N[3];
       int dA;
@@ -164,11 +174,14 @@ __global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __res
 }
 
 template <int DIM>
-__global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t n, KG g, int D,
-                          const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
+__global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
+                          int64_t n_ub, KG g, int D, const int64_t* __restrict__ offs,
+                          uint64_t* __restrict__ out, int64_t cap) {
   constexpr int NO = Nofs<DIM>::value;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n || g.depth(k[i]) != D) return;
+  if (i >= n_ub) return;
+  const int64_t n = ctl[CTL_N];
+  if (i >= n || bal_nS(ctl, cap) == 0 || g.depth(k[i]) != D) return;
   int64_t o = offs[i];
   for (int oo = 0; oo < NO; ++oo) {
     uint32_t N[3];
@@ -183,11 +196,21 @@ __global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t n, KG g, int D
   }
 }
 
-// Sort of a small key set inside one block: bitonic network over a power-of-two padded array in
-// shared memory (padding = all-ones keys, which sort last and are not written back).
+// Sort of the generated octants (at most SMALL_SORT_MAX) inside one block: bitonic network over a
+// power-of-two padded array in shared memory (padding = all-ones keys, which sort last and are
+// not written back).  Exchanges closer than 32 elements stay inside one warp and need only a
+// warp barrier.  Also the capacity check of the pass: an oversized pass is recorded, not sorted.
 constexpr int SMALL_SORT_MAX = 4096;
-__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t n) {
+__global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t* __restrict__ ctl,
+                                                     int64_t cap, int D) {
   __shared__ uint64_t sk[SMALL_SORT_MAX];
+  if (ctl[CTL_OVER] != 0) return;
+  const int64_t n = ctl[CTL_G];
+  if (n > cap || n > SMALL_SORT_MAX) {
+    if (threadIdx.x == 0) ctl[CTL_OVER] = D;
+    return;
+  }
+  if (n == 0) return;
   int P = 1;
   while (P < n) P <<= 1;
   for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < n ? keys[i] : ~0ull;
@@ -205,7 +228,11 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys
           }
         }
       }
-      __syncthreads();
+      const int next_j = j > 1 ? j >> 1 : k;  // partner distance of the next stage
+      if (j >= 32 || next_j >= 32)
+        __syncthreads();
+      else
+        __syncwarp();
     }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = sk[i];
@@ -223,11 +250,18 @@ __device__ __forceinline__ bool lin_keep(const uint64_t* __restrict__ S, int64_t
   return !(a == b || is_ancestor<DIM>(g, a, b));
 }
 template <int DIM>
-__global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t n,
-                              const uint64_t* __restrict__ S, int64_t nS, KG g,
+__global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl,
+                              int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
                               int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n_ub) return;
+  const int64_t nS = bal_nS(ctl, cap);
+  if (i == 0 && nS > 0) ctl[CTL_PASSES] += 1;  // a pass that changes the tree
+  if (i >= ctl[CTL_N]) {
+    cnt[i] = 0;
+    lo_out[i] = -1;
+    return;
+  }
   uint64_t key = k[i];
   int64_t lo = lower_bound_dev(S, nS, key);
   int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
@@ -239,19 +273,22 @@ __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t n,
   cnt[i] = c;
   lo_out[i] = hi > lo ? lo : -1;  // -1: the leaf is kept as it is
 }
+// runs after the merged count has replaced ctl[CTL_N]: rows past the old count have cnt 0
 template <int DIM>
-__global__ void k_merge_write(const uint64_t* __restrict__ k, int64_t n,
-                              const uint64_t* __restrict__ S, int64_t nS, KG g,
+__global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
+                              int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
                               const int32_t* __restrict__ cnt, const int64_t* __restrict__ lo,
                               const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n_ub) return;
+  const int c = cnt[i];
+  if (c == 0) return;
   int64_t o = offs[i], l = lo[i];
   if (l < 0) {
     out[o] = k[i];
     return;
   }
-  const int64_t end = o + cnt[i];
+  const int64_t nS = bal_nS(ctl, cap), end = o + c;
   for (int64_t r = l; o < end; ++r)
     if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
 }
@@ -259,10 +296,10 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, int64_t n,
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
 template <int DIM>
 __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64_t* __restrict__ nw,
-                      int64_t nn, KG g, int32_t* __restrict__ src, int8_t* __restrict__ tag,
-                      int32_t* bad) {
+                      int64_t nn_ub, const int64_t* __restrict__ d_nn, KG g, int32_t* __restrict__ src,
+                      int8_t* __restrict__ tag, int32_t* bad) {
   int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (j >= nn) return;
+  if (j >= nn_ub || (d_nn && j >= *d_nn)) return;
   uint64_t key = nw[j];
   int64_t B = lower_bound_dev(old, no, key);
   if (B < no && old[B] == key) {
@@ -289,11 +326,13 @@ __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64
 
 // Face connectivity (Sec. 3.3): same-depth face-neighbour box, point location of its anchor.
 template <int DIM>
-__global__ void k_conn(const uint64_t* __restrict__ k, int64_t n, KG g, int32_t* __restrict__ nbr,
-                       int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
+__global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64_t* __restrict__ d_n, KG g,
+                       int32_t* __restrict__ nbr, int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
                        int32_t* __restrict__ contrib, int32_t* bad) {
   constexpr int NFC = 2 * DIM;
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= n_ub * NFC) return;
+  const int64_t n = d_n ? *d_n : n_ub;
   if (t >= n * NFC) return;
   int64_t e = t / NFC;
   int f = int(t % NFC), axis = f >> 1, side = f & 1;
@@ -547,14 +586,14 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   int64_t* offs = S.get<int64_t>(n);
   if (!act || !cnt || !offs) return set_error(err, FR_ENOMEM, "edit scratch");
   // the edited tree has at most 2^dim leaves per old leaf: the output is sized for that bound and
-  // the leaf count stays on the device (d_ctl[0]) for the balance passes
+  // the leaf count stays on the device for the balance passes
   FR_TRY(out.ensure(A, size_t(n) << dim));
-  FR_CUDA(err, cudaMemsetAsync(d_ctl + 2, 0, 16, s));
+  FR_CUDA(err, cudaMemsetAsync(d_ctl, 0, CTL_SLOTS * sizeof(int64_t), s));
   DIM_DISPATCH(dim, (k_edit_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, d_flags, n, g, Dbase, act, cnt)));
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts(cnt, offs, n, d_ctl, S, s, err));
+  FR_TRY(scan_counts(cnt, offs, n, d_ctl + CTL_N, S, s, err));
   DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p,
-                                                               reinterpret_cast<unsigned long long*>(d_ctl + 2))));
+                                                               reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF))));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
@@ -562,21 +601,58 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
 // above this bound on the leaf count a pass first reads the exact count from the device
 constexpr int64_t BAL_UB_MAX = int64_t(1) << 19;
 
-int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl, int64_t n_ub,
-                 int64_t h_ctl[4], int* passes, Alloc& A, cudaStream_t s, Err* err) {
-  if (passes) *passes = 0;
+static int read_ctl(const int64_t* d_ctl, int64_t* h_ctl, cudaStream_t s, Err* err) {
+  if (cudaMemcpyAsync(h_ctl, d_ctl, CTL_SLOTS * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return set_error(err, FR_ECUDA, "balance count read");
+  return 0;
+}
+
+// one pass at depth D: count, scan, generate, sort, merge; octants beyond `cap` overflow the
+// pass (small sort only).  `exact_G` >= 0: the host knows the generated count (sizes from it).
+static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<uint64_t>& out,
+                        Buf<uint64_t>& gen, Buf<uint64_t>& tmp, int64_t* d_ctl, int64_t n_ub,
+                        int64_t exact_G, int64_t cap, const int32_t* cnt, const int64_t* offs,
+                        Alloc& A, cudaStream_t s, Err* err) {
+  Scratch S(&A);
+  const int64_t G_ub = exact_G >= 0 ? exact_G : cap;
+  FR_TRY(gen.ensure(A, size_t(G_ub)));
+  FR_TRY(out.ensure(A, size_t(n_ub + G_ub)));
+  DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
+  FR_LAUNCH_CHECK(err);
+  if (exact_G < 0 || exact_G <= SMALL_SORT_MAX) {
+    k_sort_small<<<1, 1024, 0, s>>>(gen.p, d_ctl, cap, D);
+    FR_LAUNCH_CHECK(err);
+  } else {
+    FR_TRY(tmp.ensure(A, size_t(exact_G)));
+    FR_TRY(radix_sort_keys(gen.p, tmp.p, exact_G, dim * g.Dmax + g.mb, S, s, err));
+  }
+  int32_t* cnt2 = S.get<int32_t>(n_ub);
+  int64_t* lo = S.get<int64_t>(n_ub);
+  int64_t* offs2 = S.get<int64_t>(n_ub);
+  if (!cnt2 || !lo || !offs2) return set_error(err, FR_ENOMEM, "balance merge scratch");
+  DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo)));
+  FR_LAUNCH_CHECK(err);
+  // the merged tree has at most n + G leaves; its count replaces ctl[CTL_N] on the device
+  FR_TRY(scan_counts(cnt2, offs2, n_ub, d_ctl + CTL_N, S, s, err));
+  DIM_DISPATCH(dim, (k_merge_write<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo, offs2, out.p)));
+  FR_LAUNCH_CHECK(err);
+  Buf<uint64_t> t = keys;  // the merged tree becomes the tree
+  keys = out;
+  out = t;
+  return 0;
+}
+
+int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
+                 int64_t n_ub, int64_t* h_ctl, Alloc& A, cudaStream_t s, Err* err) {
   Buf<uint64_t> gen, tmp, out;
   int rc = 0;
-  bool known = false;  // h_ctl[0] holds the current leaf count
-  for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
+  bool known = false;  // h_ctl holds the current control block
+  for (int D = Dhigh; D >= Dlow && D >= 2; --D) {
     if (!known && n_ub > BAL_UB_MAX) {
       // large trees: counting and scanning up to a loose bound costs more than a synchronisation
-      if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-          cudaStreamSynchronize(s) != cudaSuccess) {
-        rc = set_error(err, FR_ECUDA, "balance count read");
-        break;
-      }
-      n_ub = h_ctl[0];
+      if ((rc = read_ctl(d_ctl, h_ctl, s, err))) break;
+      n_ub = h_ctl[CTL_N];
     }
     Scratch S(&A);
     int32_t* cnt = S.get<int32_t>(n_ub);
@@ -588,55 +664,44 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d
     DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + 1, S, s, err))) break;
+    if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + CTL_G, S, s, err))) break;
     // the pass's one synchronisation: leaf count, generated count (and the edit's statistics)
-    if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      rc = set_error(err, FR_ECUDA, "balance count read");
-      break;
-    }
+    if ((rc = read_ctl(d_ctl, h_ctl, s, err))) break;
     known = true;
-    const int64_t n = h_ctl[0], G = h_ctl[1];
+    const int64_t n = h_ctl[CTL_N], G = h_ctl[CTL_G];
     n_ub = n;
     if (G == 0) continue;
-    if (passes) ++*passes;
-    if ((rc = gen.ensure(A, size_t(G))) || (rc = tmp.ensure(A, size_t(G))) || (rc = out.ensure(A, size_t(n + G))))
-      break;
-    DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, g, D, offs, gen.p)));
-    ++launch_counter();
-    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_gen") : 0)) break;
-    if (G <= SMALL_SORT_MAX) {
-      k_sort_small<<<1, 1024, 0, s>>>(gen.p, G);
-      ++launch_counter();
-      if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_sort_small") : 0)) break;
-    } else if ((rc = radix_sort_keys(gen.p, tmp.p, G, dim * g.Dmax + g.mb, S, s, err))) {
-      break;
-    }
-    int32_t* cnt2 = S.get<int32_t>(n);
-    int64_t* lo = S.get<int64_t>(n);
-    int64_t* offs2 = S.get<int64_t>(n);
-    if (!cnt2 || !lo || !offs2) {
-      rc = set_error(err, FR_ENOMEM, "balance merge scratch");
-      break;
-    }
-    DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, gen.p, G, g, cnt2, lo)));
-    ++launch_counter();
-    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_count") : 0)) break;
-    // the merged tree has at most n + G leaves; its count goes to d_ctl[0] on the device
-    if ((rc = scan_counts(cnt2, offs2, n, d_ctl, S, s, err))) break;
-    DIM_DISPATCH(dim, (k_merge_write<D_><<<nblk(n), TB, 0, s>>>(keys.p, n, gen.p, G, g, cnt2, lo, offs2, out.p)));
-    ++launch_counter();
-    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_merge_write") : 0)) break;
-    Buf<uint64_t> t = keys;  // the merged tree becomes the tree
-    keys = out;
-    out = t;
+    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, cnt, offs, A, s, err))) break;
     n_ub = n + G;
     known = false;
   }
-  if (!rc && !known) {
-    if (cudaMemcpyAsync(h_ctl, d_ctl, 4 * sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      rc = set_error(err, FR_ECUDA, "balance count read");
+  if (!rc && !known) rc = read_ctl(d_ctl, h_ctl, s, err);
+  gen.release(A);
+  tmp.release(A);
+  out.release(A);
+  return rc;
+}
+
+int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
+                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err) {
+  Buf<uint64_t> gen, tmp, out;
+  int rc = 0;
+  for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
+    Scratch S(&A);
+    const int64_t nb = *n_ub;
+    int32_t* cnt = S.get<int32_t>(nb);
+    int64_t* offs = S.get<int64_t>(nb);
+    if (!cnt || !offs) {
+      rc = set_error(err, FR_ENOMEM, "balance scratch");
+      break;
+    }
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(nb), TB, 0, s>>>(keys.p, d_ctl, nb, g, D, cnt)));
+    ++launch_counter();
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
+    if ((rc = scan_counts(cnt, offs, nb, d_ctl + CTL_G, S, s, err))) break;
+    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, nb, -1, SMALL_SORT_MAX, cnt, offs, A, s, err)))
+      break;
+    *n_ub = nb + SMALL_SORT_MAX;
   }
   gen.release(A);
   tmp.release(A);
@@ -645,19 +710,19 @@ int tree_balance(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d
 }
 
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
-             int64_t n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad, cudaStream_t s, Err* err) {
+             int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,
+             cudaStream_t s, Err* err) {
   if (n_new <= 0) return 0;
-  DIM_DISPATCH(dim, (k_map<D_><<<nblk(n_new), TB, 0, s>>>(d_old, n_old, d_new, n_new, g, d_src, d_tag, d_bad)));
+  DIM_DISPATCH(dim, (k_map<D_><<<nblk(n_new), TB, 0, s>>>(d_old, n_old, d_new, n_new, d_n_new, g, d_src, d_tag, d_bad)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
-
-int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int32_t* d_nbr,
+int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
               Err* err) {
   if (n <= 0) return 0;
   int64_t T = n * 2 * dim;
-  DIM_DISPATCH(dim, (k_conn<D_><<<nblk(T), TB, 0, s>>>(d_keys, n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
+  DIM_DISPATCH(dim, (k_conn<D_><<<nblk(T), TB, 0, s>>>(d_keys, n, d_n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -111,3 +111,28 @@ def test_extreme_degrees(p):
         o.adapt(fo)
         assert np.array_equal(g.leaves(), o.leaves())
     assert rel_l2(g.state(), o.state()) < 1e-10
+
+
+def test_balance_pass_beyond_octant_capacity():
+    # Left half of the periodic square at depth 8, right half at depth 7 (balanced); refining every
+    # depth-8 leaf puts depth-9 leaves against depth-7 ones along both interfaces, so one balance
+    # pass generates ~1.2e4 octants: more than an adaptation issued without host synchronisation
+    # holds per pass (4096), which then finishes that pass and the rest with exact sizes.
+    cfg = _cfg("vortex2d_p2_small", Dbase=6, Dmax=9)
+    boxes = [(8, x, y, 0) for x in range(0, 256, 2) for y in range(0, 512, 2)]
+    boxes += [(7, x, y, 0) for x in range(256, 512, 4) for y in range(0, 512, 4)]
+    keys = np.sort(O.morton_encode(2, 9, np.array(boxes)))
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    u = 1.0 + 0.1 * W.random_uniform(len(keys) * g.nv * g.N, 17).reshape(len(keys), g.nv, g.N)
+    g.set_state(keys, u)
+    o.set_state(keys, u)
+    depth = (keys & np.uint64(15)).astype(np.int64)
+    flags = np.where(depth == 8, 1, 0).astype(np.int8)
+    st = g.adapt(flags, stats=True)
+    o.adapt(flags)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert st["M_new"] == len(o.leaves()) and st["n_refined"] == 32768
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    for a, b in zip(g.conn(), O.conn(2, 9, o.leaves())):
+        assert np.array_equal(a, b)
