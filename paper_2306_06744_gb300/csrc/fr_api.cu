@@ -33,6 +33,7 @@ struct fr_mesh {
   Buf<double> norm_part, norm_out;
   Buf<unsigned long long> dmax;
   Buf<float> mlp_params;  // learned indicator weights (FP32 master copy), empty if none
+  Buf<int32_t> status;    // device word set by a tensor-core kernel whose completion wait gave up
   int64_t mlp_n = 0;
   // measurement: event pairs around interface (kind 0) and element (kind 1) launches
   struct Rec {
@@ -288,7 +289,7 @@ int compute_flags(fr_mesh* m, double* eta) {
     if (!X) return set_error(&m->err, FR_ENOMEM, "feature scratch");
     FR_TRY(mlp_features(m->dim, m->p, m->u.p, m->keys.p, m->M, m->g, m->cfg.Dbase, m->cfg.gamma,
                         m->ops, X, m->stream, &m->err));
-    return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->stream, &m->err);
+    return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->status.p, m->stream, &m->err);
   }
   // density gradient (indicator 0, and the fallback of the learned indicator) or analytic centre
   return launch_indicator(m->dim, m->p, m->cfg.indicator == 1 ? 1 : 0, m->cfg.th_refine, m->cfg.th_coarsen,
@@ -345,7 +346,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   int32_t* bad = Sc.get<int32_t>(2);
   if (!ctl || !bad) return set_error(err, FR_ENOMEM, "adapt scratch");
   int64_t h_ctl[CTL_SLOTS] = {0};
-  int32_t hb[2] = {0, 0};
+  int32_t hb[2] = {0, 0}, hs = 0;
   Buf<uint64_t> nk;
   Buf<double> nu;
   Buf<int32_t> src, hcon;
@@ -370,8 +371,10 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     if (!r) r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon);
     if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaMemcpyAsync(&hs, m->status.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaStreamSynchronize(s) != cudaSuccess))
       r = set_error(err, FR_ECUDA, "adapt read");
+    if (!r && hs) r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator)");
     return r;
   };
   if (!rc && fast) {
@@ -477,6 +480,8 @@ int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void*
   }
   // uniform tree at Dbase, then passes of {closed form, flags, adapt}
   m->M = int64_t(1) << (m->dim * cfg->Dbase);
+  FR_TRY(m->status.ensure(m->A, 1));
+  FR_CUDA(err, cudaMemsetAsync(m->status.p, 0, 4, m->stream));
   FR_TRY(m->keys.ensure(m->A, m->M));
   FR_TRY(tree_uniform(m->dim, m->g, cfg->Dbase, m->keys.p, m->stream, err));
   FR_TRY(ensure_state(m, m->M));
@@ -526,6 +531,7 @@ void free_all(fr_mesh* m) {
   m->norm_out.release(m->A);
   m->dmax.release(m->A);
   m->mlp_params.release(m->A);
+  m->status.release(m->A);
   m->A.release_cache();
   // blocks still handed out (none after a clean release) go back to the allocator as well
   auto live = m->cache.live;
@@ -825,16 +831,24 @@ int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n) {
 
 int fr_mlp_forward(int in_dim, const float* d_params, const void* d_X, int64_t n, float* d_logits,
                    int8_t* d_flags, void* stream) {
-  if (in_dim < 1 || in_dim > 4096 || n < 0) return set_error(global_err(), FR_EINVAL, "bad arguments");
+  if (in_dim < 1 || in_dim > 64 || n < 0) return set_error(global_err(), FR_EINVAL, "bad arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  FR_TRY(mlp_forward(d_params, in_dim, d_X, n, d_logits, d_flags, s, global_err()));
+  Alloc A{nullptr, s, global_err()};
+  Scratch S(&A);
+  int* st = S.get<int>(1);
+  if (!st) return set_error(global_err(), FR_ENOMEM, "scratch");
+  FR_CUDA(global_err(), cudaMemsetAsync(st, 0, 4, s));
+  FR_TRY(mlp_forward(d_params, in_dim, d_X, n, d_logits, d_flags, st, s, global_err()));
+  int hs = 0;
+  FR_CUDA(global_err(), cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s));
   FR_CUDA(global_err(), cudaStreamSynchronize(s));
+  if (hs) return set_error(global_err(), FR_ETIMEOUT, "a tensor-core completion wait gave up");
   return 0;
 }
 
 int fr_mlp_grad(int in_dim, const float* d_params, const void* d_X, const int8_t* d_y, int64_t B,
                 const float* class_w, float* d_grad, float* d_loss, void* stream) {
-  if (in_dim < 1 || in_dim > 4096 || B <= 0 || !class_w)
+  if (in_dim < 1 || in_dim > 64 || B <= 0 || !class_w)
     return set_error(global_err(), FR_EINVAL, "bad arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Alloc A{nullptr, s, global_err()};
@@ -846,7 +860,7 @@ int fr_mlp_grad(int in_dim, const float* d_params, const void* d_X, const int8_t
 int fr_mlp_train_step(int in_dim, float* d_params, float* d_m, float* d_v, int64_t step,
                       const void* d_X, const int8_t* d_y, int64_t B, const float* class_w, float lr,
                       float* d_loss, void* stream) {
-  if (in_dim < 1 || in_dim > 4096 || B <= 0 || !class_w || step < 0)
+  if (in_dim < 1 || in_dim > 64 || B <= 0 || !class_w || step < 0)
     return set_error(global_err(), FR_EINVAL, "bad arguments");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   Alloc A{nullptr, s, global_err()};

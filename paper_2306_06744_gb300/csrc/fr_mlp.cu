@@ -10,15 +10,17 @@
 // relative deviations from their means scaled by 100 (a 1% variation is 1.0), then the depth as
 // (D - Dbase) / max(1, Dmax - Dbase): IN = 2*3^dim + 1 inputs (19 in 2D, 55 in 3D).
 //
-// The contractions are 64 wide and cost about 12k multiply-adds per element, well under 0.1% of a
-// time step of the FR solver for the same element, so they run on the CUDA cores (FP32 FMA on
-// BF16-rounded operands); the weights sit in shared memory and are read by broadcast.
+// Inference runs on the tensor cores (tcgen05, BF16 operands in shared memory, FP32 accumulators
+// in tensor memory): batched over elements the layers are dense [128 x 64] x [64 x 64]
+// contractions.  Training (per-sample forward/backward and the weight-gradient reduction) runs on
+// the CUDA cores with FP32 FMA on BF16-rounded operands.
 #include <cuda_bf16.h>
 
 #include <cmath>
 
 #include "fr_internal.cuh"
 #include "fr_mlp.cuh"
+#include "fr_tc.cuh"
 
 namespace frg {
 
@@ -147,31 +149,194 @@ __device__ __forceinline__ void layer_out(const float* W, const float* b, const 
   }
 }
 
-__global__ void __launch_bounds__(MLP_T) k_mlp_forward(const float* __restrict__ P, int in,
-                                                       const __nv_bfloat16* __restrict__ X,
-                                                       int64_t n, float* __restrict__ logits,
-                                                       int8_t* __restrict__ flags) {
-  extern __shared__ float sw[];
+// Tensor-core forward.  Each block keeps the four weight matrices in shared memory as BF16 in the
+// K-major core-matrix layout of fr_tc.cuh (W1 zero-padded to 64 inputs, W4 to 16 outputs) and
+// loops over tiles of 128 samples.  The tile's feature rows are one contiguous block, fetched by a
+// bulk copy into one of two staging buffers while the previous tile is computed.  Per tile the
+// rows are rewritten into the activation tile A; per layer one thread issues the K/16 MMAs of
+// A * W^T into a 128 x 64 FP32 accumulator in tensor memory and commits them to an mbarrier; once
+// it completes, thread r reads row r of the accumulator (TMEM lane r), adds the bias, applies
+// GELU, rounds to BF16 and writes the row back into A as the next layer's operand.  The output
+// layer (N = 16, 3 used) gives the logits and the argmax flag.  A wait that does not complete
+// within about a second sets *status, waits once more (bounded) for the copies and MMAs in
+// flight, frees the tensor memory and ends the block.
+constexpr int TC_ROWS = 128, TC_TMEM_COLS = 64;
+constexpr long long TC_WAIT_CYCLES = 2000000000ll;
+constexpr int TC_W1 = 0, TC_W2 = 8192, TC_W3 = 16384, TC_W4 = 24576, TC_A = 26624, TC_X0 = 43008,
+              TC_X1 = TC_X0 + 16384, TC_BIAS = TC_X1 + 16384, TC_MBAR = TC_BIAS + 208 * 4,
+              TC_SMEM = TC_MBAR + 32 + 1024;
+
+__global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restrict__ P, int in,
+                                                            const __nv_bfloat16* __restrict__ X, int64_t n,
+                                                            float* __restrict__ logits,
+                                                            int8_t* __restrict__ flags, int* __restrict__ status) {
+  extern __shared__ unsigned char sm_raw[];
+  // 1024-byte aligned base for the operand tiles
+  unsigned char* sm = sm_raw + ((1024 - (tc::smem_addr(sm_raw) & 1023)) & 1023);
+  const int t = threadIdx.x, warp = t >> 5;
   const Lay L = lay(in);
-  load_weights(P, L.total, sw);
+  const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+  const uint32_t mb = tc::smem_addr(sm + TC_MBAR);  // MMA completion
+  const uint32_t fb[2] = {mb + 8, mb + 16};         // feature copies into the staging buffers
+  const int xoff[2] = {TC_X0, TC_X1};
+  // a tile is fetched by a bulk copy when it is full (its 256*in bytes start 16-byte aligned when
+  // X does); the last, partial tile is read by the threads
+  const bool bulk_ok = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  auto tile_bulk = [&](int64_t tile) { return bulk_ok && (tile + 1) * TC_ROWS <= n; };
+  auto fetch = [&](int64_t tile, int b) {
+    tc::fence_proxy_async();
+    tc::bulk_g2s(tc::smem_addr(sm + xoff[b]), X + tile * TC_ROWS * in, uint32_t(TC_ROWS * in * 2), fb[b]);
+  };
+  // copies in flight per staging buffer (the issue conditions are uniform over the block)
+  bool pend[2] = {blockIdx.x < ntiles && tile_bulk(blockIdx.x), false};
+  if (t == 0) {
+    tc::mbar_init(mb, 1);
+    tc::mbar_init(fb[0], 1);
+    tc::mbar_init(fb[1], 1);
+    if (pend[0]) fetch(blockIdx.x, 0);
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(sm + TC_MBAR + 24), TC_TMEM_COLS);
+  auto put = [&](int off, int r, int k, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(sm + off + tc::canon_off(r, k)) = __float2bfloat16_rn(v);
+  };
+  for (int idx = t; idx < H * 64; idx += TC_ROWS) {
+    const int o = idx >> 6, k = idx & 63;
+    put(TC_W1, o, k, k < in ? P[L.oW1 + o * in + k] : 0.f);
+    put(TC_W2, o, k, P[L.oW2 + o * H + k]);
+    put(TC_W3, o, k, P[L.oW3 + o * H + k]);
+    if (o < 16) put(TC_W4, o, k, o < NOUT ? P[L.oW4 + o * H + k] : 0.f);
+  }
+  float* sb = reinterpret_cast<float*>(sm + TC_BIAS);  // b1 | b2 | b3 | b4 (16), BF16-rounded
+  for (int i = t; i < H; i += TC_ROWS) {
+    sb[i] = bf16r(P[L.ob1 + i]);
+    sb[H + i] = bf16r(P[L.ob2 + i]);
+    sb[2 * H + i] = bf16r(P[L.ob3 + i]);
+  }
+  if (t < 16) sb[3 * H + t] = t < NOUT ? bf16r(P[L.ob4 + t]) : 0.f;
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
   __syncthreads();
-  int64_t b = int64_t(blockIdx.x) * MLP_T + threadIdx.x;
-  if (b >= n) return;
-  float z[H], a[H], o[NOUT];
-  layer_in(sw + L.oW1, sw + L.ob1, X + b * in, in, z);
-  act(z, a);
-  layer_h(sw + L.oW2, sw + L.ob2, a, z);
-  act(z, a);
-  layer_h(sw + L.oW3, sw + L.ob3, a, z);
-  act(z, a);
-  layer_out(sw + L.oW4, sw + L.ob4, a, o);
-  if (logits)
-    for (int c = 0; c < NOUT; ++c) logits[b * NOUT + c] = o[c];
-  if (flags) {
-    int best = 0;
-    for (int c = 1; c < NOUT; ++c)
-      if (o[c] > o[best]) best = c;
-    flags[b] = int8_t(best - 1);  // class 0 coarsen, 1 keep, 2 refine
+  tc::fence_after_sync();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TC_MBAR + 24);
+  const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);  // this warp's 32 TMEM lanes
+  const uint32_t sA = tc::smem_addr(sm + TC_A);
+  const int K1 = in <= 32 ? 32 : 64;
+  uint32_t phase = 0, fphase[2] = {0, 0};
+  bool failed = false, mma_pend = false;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
+    const int b = it & 1;
+    const int64_t row0 = tile * TC_ROWS;
+    const int nrow = int(n - row0 < TC_ROWS ? n - row0 : TC_ROWS);
+    const unsigned char* xs;  // this tile's rows, contiguous BF16
+    if (pend[b]) {
+      const bool ok = tc::mbar_wait(fb[b], fphase[b], TC_WAIT_CYCLES);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      fphase[b] ^= 1;
+      pend[b] = false;
+      xs = sm + xoff[b];
+    } else {
+      xs = reinterpret_cast<const unsigned char*>(X + row0 * in);
+    }
+    // the next tile of this block goes into the other staging buffer, read in the last iteration
+    if (tile + gridDim.x < ntiles && tile_bulk(tile + gridDim.x)) {
+      pend[b ^ 1] = true;
+      if (t == 0) fetch(tile + gridDim.x, b ^ 1);
+    }
+    // row t of the tile -> row t of A (zero rows past the end, zero columns past `in`)
+    {
+      const __nv_bfloat16* xr = reinterpret_cast<const __nv_bfloat16*>(xs) + t * in;
+      for (int k0 = 0; k0 < K1; k0 += 8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = k0 + 2 * j;
+          __nv_bfloat162 h2;
+          h2.x = (t < nrow && k < in) ? xr[k] : __float2bfloat16_rn(0.f);
+          h2.y = (t < nrow && k + 1 < in) ? xr[k + 1] : __float2bfloat16_rn(0.f);
+          pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(sm + TC_A + tc::canon_off(t, k0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    for (int layer = 0; layer < 4; ++layer) {
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (t == 0) {
+        tc::fence_after_sync();
+        const int nk = layer == 0 ? K1 / 16 : H / 16;
+        const uint32_t sW = tc::smem_addr(sm + (layer == 0 ? TC_W1 : layer == 1 ? TC_W2 : layer == 2 ? TC_W3 : TC_W4));
+        const uint32_t id = tc::idesc_bf16(TC_ROWS, layer == 3 ? 16 : H);
+        for (int ks = 0; ks < nk; ++ks)
+          tc::mma_bf16(tmem, tc::sdesc(sA + ks * 2 * tc::LBO), tc::sdesc(sW + ks * 2 * tc::LBO), id, ks > 0);
+        tc::commit(mb);
+      }
+      mma_pend = true;
+      const bool ok = tc::mbar_wait(mb, phase, TC_WAIT_CYCLES);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      phase ^= 1;
+      mma_pend = false;
+      tc::fence_after_sync();
+      if (layer < 3) {
+        const float* bl = sb + H * layer;
+        uint32_t r[4][16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tc::tmem_ld16(tlane + uint32_t(16 * q), r[q]);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint32_t pk[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int c = 16 * q + 2 * j;
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(gelu(__uint_as_float(r[q][2 * j]) + bl[c]),
+                                                      gelu(__uint_as_float(r[q][2 * j + 1]) + bl[c + 1]));
+            pk[j] = *reinterpret_cast<uint32_t*>(&h2);
+          }
+          *reinterpret_cast<uint4*>(sm + TC_A + tc::canon_off(t, 16 * q)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          *reinterpret_cast<uint4*>(sm + TC_A + tc::canon_off(t, 16 * q + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+      } else {
+        uint32_t r[16];
+        tc::tmem_ld16(tlane, r);
+        tc::tmem_wait_ld();
+        if (t < nrow) {
+          const int64_t row = row0 + t;
+          float o[NOUT];
+#pragma unroll
+          for (int c = 0; c < NOUT; ++c) o[c] = __uint_as_float(r[c]) + sb[3 * H + c];
+          if (logits)
+            for (int c = 0; c < NOUT; ++c) logits[row * NOUT + c] = o[c];
+          if (flags) {
+            int best = 0;
+            for (int c = 1; c < NOUT; ++c)
+              if (o[c] > o[best]) best = c;
+            flags[row] = int8_t(best - 1);  // class 0 coarsen, 1 keep, 2 refine
+          }
+        }
+      }
+    }
+  }
+  if (failed) {
+    if (t == 0) atomicExch(status, 1);
+    // bounded waits for what may still be in flight (the block's shared memory must not be
+    // released under a copy): the MMAs of the failed wait and the pending feature copies
+    if (mma_pend) tc::mbar_wait(mb, phase, TC_WAIT_CYCLES);
+    for (int q = 0; q < 2; ++q)
+      if (pend[q]) tc::mbar_wait(fb[q], fphase[q], TC_WAIT_CYCLES);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, TC_TMEM_COLS);
   }
 }
 
@@ -342,12 +507,26 @@ size_t fwd_smem(int in) { return sizeof(float) * size_t(lay(in).total); }
 int mlp_param_count(int in) { return lay(in).total; }
 
 int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float* d_logits,
-                int8_t* d_flags, cudaStream_t s, Err* err) {
+                int8_t* d_flags, int* d_status, cudaStream_t s, Err* err) {
+  if (in < 1 || in > 64) return set_error(err, FR_EINVAL, "the MLP takes 1..64 inputs");
   if (n <= 0) return 0;
-  size_t sm = fwd_smem(in);
-  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  k_mlp_forward<<<unsigned((n + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
-      d_params, in, static_cast<const __nv_bfloat16*>(d_X), n, d_logits, d_flags);
+  static int grid_cap[64] = {0};  // blocks of the persistent grid, per device
+  int dev = 0;
+  FR_CUDA(err, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return set_error(err, FR_ECUDA, "device index");
+  if (grid_cap[dev] == 0) {
+    FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    int sms = 0, per = 0;
+    FR_CUDA(err, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FR_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_forward_tc, TC_ROWS, TC_SMEM));
+    // every resident block holds TC_TMEM_COLS of the SM's 512 tensor-memory columns
+    if (per > 512 / TC_TMEM_COLS) per = 512 / TC_TMEM_COLS;
+    grid_cap[dev] = sms * (per > 0 ? per : 1);
+  }
+  const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
+  const unsigned grid = unsigned(ntiles < grid_cap[dev] ? ntiles : grid_cap[dev]);
+  k_mlp_forward_tc<<<grid, TC_ROWS, TC_SMEM, s>>>(d_params, in, static_cast<const __nv_bfloat16*>(d_X), n,
+                                                  d_logits, d_flags, d_status);
   FR_LAUNCH_CHECK(err);
   return 0;
 }
