@@ -41,7 +41,7 @@ extern "C" {
 #define FR_EINVAL (-1)    /* bad argument, layout or configuration                        */
 #define FR_ENOMEM (-2)    /* device allocation failed                                       */
 #define FR_EOVERFLOW (-3) /* caller capacity too small (required size written back)        */
-#define FR_ETIMEOUT (-4)  /* a bounded device wait gave up (reserved; no kernel waits today) */
+#define FR_ETIMEOUT (-4)  /* a bounded device wait gave up (tensor-core completion, about 1 s) */
 #define FR_ECUDA (-5)     /* CUDA runtime error                                             */
 
 typedef struct fr_mesh fr_mesh;
@@ -174,7 +174,12 @@ const char* fr_last_error(const fr_mesh* m);
    1/sum_batch w_label}: the loss is sum_b w_b CE_b * class_w[3] (weighted mean cross-entropy).
    fr_mlp_train_step performs one Adam step (beta 0.9/0.999, eps 1e-8; d_m, d_v the moment arrays,
    step counts from 0) in place on d_params; d_loss (device, may be NULL) receives the batch loss.
-   fr_mlp_grad returns the gradient of that loss instead.  Device pointers throughout. */
+   fr_mlp_grad returns the gradient of that loss instead.  Device pointers throughout; 1 <= IN <= 64
+   (FR_EINVAL otherwise).
+   fr_mlp_forward (and the mesh's learned indicator) runs on the tensor cores: BF16 MMAs with FP32
+   accumulators in tensor memory, over tiles of 128 feature rows; a completion wait that gives up
+   after about a second returns FR_ETIMEOUT (from fr_adapt/fr_run when it happens inside the
+   indicator).  Training runs on the CUDA cores. */
 int fr_mlp_param_count(int in_dim);
 int fr_features(fr_mesh* m, void* d_X_bf16, int64_t cap, int32_t* in_dim);
 int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n);

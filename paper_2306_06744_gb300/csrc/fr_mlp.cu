@@ -64,44 +64,86 @@ struct I3Mat {
   double m[3][NPMAX];
 };
 
+// One thread per element.  The interpolation to the 3^dim sample points is sum-factorised (one
+// axis at a time: n^dim -> 3 n^(dim-1) -> ... -> 3^dim values per variable) in FP64; density is
+// kept per sample point, the squared momentum accumulated, and pressure formed when the energy
+// arrives.  In 3D the first two axes are done per z-slice, so only 3^2 n values stay live.
 template <int DIM, int NP>
-__global__ void k_features(const double* __restrict__ u, const uint64_t* __restrict__ keys,
-                           int64_t M, KG g, int Dbase, double gamma, const __grid_constant__ I3Mat I3,
-                           __nv_bfloat16* __restrict__ X) {
+__global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, const uint64_t* __restrict__ keys,
+                                                  int64_t M, KG g, int Dbase, double gamma,
+                                                  const __grid_constant__ I3Mat I3, __nv_bfloat16* __restrict__ X) {
   constexpr int N = DIM == 2 ? NP * NP : NP * NP * NP;
-  constexpr int S = DIM == 2 ? 9 : 27;  // sample points
+  constexpr int NZ = DIM == 2 ? 1 : NP;  // z-slices
+  constexpr int S = DIM == 2 ? 9 : 27;   // sample points, t = s0 + 3 s1 (+ 9 s2)
   constexpr int NV = DIM + 2, IN = 2 * S + 1;
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M) return;
   const double* q = u + e * NV * N;
-  double rho[S], pr[S], rm = 0.0, pm = 0.0;
-  for (int t = 0; t < S; ++t) {
-    int s0 = t % 3, s1 = (t / 3) % 3, s2 = DIM == 3 ? t / 9 : 0;
-    double qv[NV];
-    for (int v = 0; v < NV; ++v) {
-      double acc = 0.0;
-      for (int i = 0; i < N; ++i) {
-        int i0 = i % NP, i1 = (i / NP) % NP, i2 = DIM == 3 ? i / (NP * NP) : 0;
-        double w = I3.m[s0][i0] * I3.m[s1][i1];
-        if (DIM == 3) w *= I3.m[s2][i2];
-        acc += w * q[v * N + i];
+  double rho[S], ke[S];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    // b[i2][s1][s0] = sum_i1 I[s1][i1] sum_i0 I[s0][i0] q[i2][i1][i0]
+    double b[NZ][3][3];
+#pragma unroll
+    for (int i2 = 0; i2 < NZ; ++i2) {
+      double a[NP][3];
+#pragma unroll
+      for (int i1 = 0; i1 < NP; ++i1) {
+        double x[NP];
+#pragma unroll
+        for (int i0 = 0; i0 < NP; ++i0) x[i0] = q[v * N + (i2 * NP + i1) * NP + i0];
+#pragma unroll
+        for (int s0 = 0; s0 < 3; ++s0) {
+          double acc = 0.0;
+#pragma unroll
+          for (int i0 = 0; i0 < NP; ++i0) acc = fma(I3.m[s0][i0], x[i0], acc);
+          a[i1][s0] = acc;
+        }
       }
-      qv[v] = acc;
+#pragma unroll
+      for (int s1 = 0; s1 < 3; ++s1)
+#pragma unroll
+        for (int s0 = 0; s0 < 3; ++s0) {
+          double acc = 0.0;
+#pragma unroll
+          for (int i1 = 0; i1 < NP; ++i1) acc = fma(I3.m[s1][i1], a[i1][s0], acc);
+          b[i2][s1][s0] = acc;
+        }
     }
-    double m2 = 0.0;
-    for (int b = 0; b < DIM; ++b) m2 += qv[1 + b] * qv[1 + b];
-    double p = (gamma - 1.0) * (qv[NV - 1] - 0.5 * m2 / qv[0]);
-    rho[t] = qv[0];
-    pr[t] = p;
-    rm += qv[0];
-    pm += p;
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int s0 = t % 3, s1 = (t / 3) % 3, s2 = t / 9;
+      double c;
+      if (DIM == 2) {
+        c = b[0][s1][s0];
+      } else {
+        c = 0.0;
+#pragma unroll
+        for (int i2 = 0; i2 < NZ; ++i2) c = fma(I3.m[s2][i2], b[i2][s1][s0], c);
+      }
+      if (v == 0) {
+        rho[t] = c;
+        ke[t] = 0.0;
+      } else if (v < NV - 1) {
+        ke[t] = fma(c, c, ke[t]);
+      } else {
+        ke[t] = (gamma - 1.0) * (c - 0.5 * ke[t] / rho[t]);  // pressure
+      }
+    }
+  }
+  double rm = 0.0, pm = 0.0;
+#pragma unroll
+  for (int t = 0; t < S; ++t) {
+    rm += rho[t];
+    pm += ke[t];
   }
   rm /= S;
   pm /= S;
   __nv_bfloat16* x = X + e * IN;
+#pragma unroll
   for (int t = 0; t < S; ++t) {
     x[t] = __float2bfloat16_rn(float(100.0 * (rho[t] - rm) / rm));
-    x[S + t] = __float2bfloat16_rn(float(100.0 * (pr[t] - pm) / pm));
+    x[S + t] = __float2bfloat16_rn(float(100.0 * (ke[t] - pm) / pm));
   }
   int span = g.Dmax - Dbase > 0 ? g.Dmax - Dbase : 1;
   x[2 * S] = __float2bfloat16_rn(float(g.depth(keys[e]) - Dbase) / float(span));

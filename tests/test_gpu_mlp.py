@@ -75,6 +75,25 @@ def test_training_learns_a_separable_rule():
     assert acc > 0.9
 
 
+@pytest.mark.parametrize("name,p,Dbase,Dmax", [("vortex2d_p3", 3, 4, 6), ("vortex2d_p2_small", 1, 3, 5),
+                                               ("vortex3d_p2_tube", 3, 2, 4), ("vortex3d_p2_tube", 4, 2, 3)])
+def test_features_parity(name, p, Dbase, Dmax):
+    cfg = W.config(name)
+    cfg.update(p=p, Dbase=Dbase, Dmax=Dmax)
+    g = fr.Mesh(cfg)
+    g.step(2)
+    X = g.features().to(__import__("torch").float64).cpu().numpy()
+    dim = cfg["dim"]
+    depths = O.morton_decode(dim, Dmax, g.leaves())[:, 0]
+    want = mlp.bf16(mlp.features(g.state(), depths, dim, p, cfg["gamma"], Dbase, Dmax,
+                                 O.operators(p)["x"]))
+    assert X.shape == want.shape == (g.M, 2 * 3 ** dim + 1)
+    # one BF16 ulp, plus an absolute floor for far-field elements where density and pressure are
+    # constant to FP64 precision: there a feature is 100 (q_i - mean q) / mean q of O(1) values
+    # summed in different orders on the two sides (up to 125 terms), i.e. noise of ~1e-14..1e-13
+    assert np.all(np.abs(X - want) <= 2.0 ** -7 * np.abs(want) + 1e-12)
+
+
 def test_features_parity_and_indicator_modes():
     cfg = W.config("vortex3d_p2_tube")
     cfg.update(Dbase=2, Dmax=4, indicator=3)
