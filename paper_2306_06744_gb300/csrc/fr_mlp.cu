@@ -204,9 +204,21 @@ __device__ __forceinline__ void layer_out(const float* W, const float* b, const 
 // flight, frees the tensor memory and ends the block.
 constexpr int TC_ROWS = 128, TC_TMEM_COLS = 64;
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;
-constexpr int TC_W1 = 0, TC_W2 = 8192, TC_W3 = 16384, TC_W4 = 24576, TC_A = 26624, TC_X0 = 43008,
-              TC_X1 = TC_X0 + 16384, TC_BIAS = TC_X1 + 16384, TC_MBAR = TC_BIAS + 208 * 4,
-              TC_SMEM = TC_MBAR + 32 + 1024;
+constexpr int TC_W1 = 0, TC_W2 = 8192, TC_W3 = 16384, TC_W4 = 24576, TC_A = 26624, TC_X0 = 43008;
+// shared-memory plan for `in` inputs: two staging buffers of 128*in BF16 (1024-byte granules),
+// then the biases, the three mbarriers and the TMEM address; plus 1024 bytes of alignment slack
+struct TcPlan {
+  int x1, bias, mbar, bytes;
+};
+__host__ __device__ inline TcPlan tc_plan(int in) {
+  const int xb = (TC_ROWS * in * 2 + 1023) / 1024 * 1024;
+  TcPlan q;
+  q.x1 = TC_X0 + xb;
+  q.bias = q.x1 + xb;
+  q.mbar = q.bias + 208 * 4;
+  q.bytes = q.mbar + 32 + 1024;
+  return q;
+}
 
 __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restrict__ P, int in,
                                                             const __nv_bfloat16* __restrict__ X, int64_t n,
@@ -217,10 +229,11 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
   unsigned char* sm = sm_raw + ((1024 - (tc::smem_addr(sm_raw) & 1023)) & 1023);
   const int t = threadIdx.x, warp = t >> 5;
   const Lay L = lay(in);
+  const TcPlan Q = tc_plan(in);
   const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
-  const uint32_t mb = tc::smem_addr(sm + TC_MBAR);  // MMA completion
-  const uint32_t fb[2] = {mb + 8, mb + 16};         // feature copies into the staging buffers
-  const int xoff[2] = {TC_X0, TC_X1};
+  const uint32_t mb = tc::smem_addr(sm + Q.mbar);  // MMA completion
+  const uint32_t fb[2] = {mb + 8, mb + 16};        // feature copies into the staging buffers
+  const int xoff[2] = {TC_X0, Q.x1};
   // a tile is fetched by a bulk copy when it is full (its 256*in bytes start 16-byte aligned when
   // X does); the last, partial tile is read by the threads
   const bool bulk_ok = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
     tc::mbar_init(fb[1], 1);
     if (pend[0]) fetch(blockIdx.x, 0);
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(sm + TC_MBAR + 24), TC_TMEM_COLS);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(sm + Q.mbar + 24), TC_TMEM_COLS);
   auto put = [&](int off, int r, int k, float v) {
     *reinterpret_cast<__nv_bfloat16*>(sm + off + tc::canon_off(r, k)) = __float2bfloat16_rn(v);
   };
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
     put(TC_W3, o, k, P[L.oW3 + o * H + k]);
     if (o < 16) put(TC_W4, o, k, o < NOUT ? P[L.oW4 + o * H + k] : 0.f);
   }
-  float* sb = reinterpret_cast<float*>(sm + TC_BIAS);  // b1 | b2 | b3 | b4 (16), BF16-rounded
+  float* sb = reinterpret_cast<float*>(sm + Q.bias);  // b1 | b2 | b3 | b4 (16), BF16-rounded
   for (int i = t; i < H; i += TC_ROWS) {
     sb[i] = bf16r(P[L.ob1 + i]);
     sb[H + i] = bf16r(P[L.ob2 + i]);
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TC_MBAR + 24);
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + Q.mbar + 24);
   const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);  // this warp's 32 TMEM lanes
   const uint32_t sA = tc::smem_addr(sm + TC_A);
   const int K1 = in <= 32 ? 32 : 64;
@@ -552,23 +565,24 @@ int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float
                 int8_t* d_flags, int* d_status, cudaStream_t s, Err* err) {
   if (in < 1 || in > 64) return set_error(err, FR_EINVAL, "the MLP takes 1..64 inputs");
   if (n <= 0) return 0;
-  static int grid_cap[64] = {0};  // blocks of the persistent grid, per device
   int dev = 0;
   FR_CUDA(err, cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return set_error(err, FR_ECUDA, "device index");
-  if (grid_cap[dev] == 0) {
-    FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    int sms = 0, per = 0;
+  const int smem = tc_plan(in).bytes;
+  static int sms = 0;
+  if (sms == 0) {
     FR_CUDA(err, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    FR_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_forward_tc, TC_ROWS, TC_SMEM));
-    // every resident block holds TC_TMEM_COLS of the SM's 512 tensor-memory columns
-    if (per > 512 / TC_TMEM_COLS) per = 512 / TC_TMEM_COLS;
-    grid_cap[dev] = sms * (per > 0 ? per : 1);
+    FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   }
+  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per = 0;
+  FR_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_forward_tc, TC_ROWS, smem));
+  // every resident block holds TC_TMEM_COLS of the SM's 512 tensor-memory columns
+  if (per > 512 / TC_TMEM_COLS) per = 512 / TC_TMEM_COLS;
+  const int64_t cap = int64_t(sms) * (per > 0 ? per : 1);
   const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
-  const unsigned grid = unsigned(ntiles < grid_cap[dev] ? ntiles : grid_cap[dev]);
-  k_mlp_forward_tc<<<grid, TC_ROWS, TC_SMEM, s>>>(d_params, in, static_cast<const __nv_bfloat16*>(d_X), n,
-                                                  d_logits, d_flags, d_status);
+  const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
+  k_mlp_forward_tc<<<grid, TC_ROWS, smem, s>>>(d_params, in, static_cast<const __nv_bfloat16*>(d_X), n,
+                                               d_logits, d_flags, d_status);
   FR_LAUNCH_CHECK(err);
   return 0;
 }

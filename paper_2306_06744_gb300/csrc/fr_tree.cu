@@ -152,54 +152,74 @@ __device__ __forceinline__ int64_t bal_nS(const int64_t* ctl, int64_t cap) {
   return (ctl[CTL_OVER] != 0 || G > cap) ? 0 : G;
 }
 
-// one thread per leaf: the leaf's requests over its 3^dim-1 neighbour boxes are counted and then
-// written consecutively, so the scan runs over leaves, not over (leaf, neighbour) pairs.  Threads
-// up to an upper bound of the leaf count write zeros past it.
+// A group of lanes per leaf (8 in 2D, a warp in 3D), one lane per neighbour box of the leaf's
+// 3^dim-1 stencil: the lanes search in parallel and combine by warp shuffles, so the scan that
+// places the generated octants runs over leaves, not over (leaf, neighbour) pairs.  Lanes past
+// the leaf count (an upper bound of it sizes the grid) contribute zeros.
+template <int DIM>
+struct BalLanes {
+  static constexpr int value = DIM == 2 ? 8 : 32;
+};
+
+// number of octants lane (i, o) generates, with the containing leaf's depth and the box
+template <int DIM>
+__device__ __forceinline__ int bal_lane(const uint64_t* __restrict__ k, int64_t n, const KG& g, int D,
+                                        int64_t i, int o, uint32_t* N, int* dA) {
+  constexpr int NO = Nofs<DIM>::value;
+  if (i >= n || o >= NO) return 0;
+  return bal_query<DIM>(k, n, g, D, i, o, N, dA) ? (D - 1 - *dA) << DIM : 0;
+}
+
 template <int DIM>
 __global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                             int64_t n_ub, KG g, int D, int32_t* __restrict__ cnt) {
-  constexpr int NO = Nofs<DIM>::value;
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_ub) return;
-  const int64_t n = ctl[CTL_N];
-  int32_t c = 0;
-  if (i < n && ctl[CTL_OVER] == 0 && g.depth(k[i]) == D) {
-    for (int o = 0; o < NO; ++o) {
-      uint32_t N[3];
-      int dA;
-      if (bal_query<DIM>(k, n, g, D, i, o, N, &dA)) c += (D - 1 - dA) << DIM;
-    }
-  }
-  cnt[i] = c;
+  constexpr int LPL = BalLanes<DIM>::value;
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = gt / LPL;
+  const int o = int(gt % LPL);
+  const int64_t n = ctl[CTL_OVER] == 0 ? ctl[CTL_N] : 0;
+  uint32_t N[3];
+  int dA = 0;
+  int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA) : 0;
+#pragma unroll
+  for (int w = LPL / 2; w > 0; w >>= 1) c += __shfl_xor_sync(0xffffffffu, c, w);
+  if (o == 0 && i < n_ub) cnt[i] = c;
 }
 
 template <int DIM>
 __global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                           int64_t n_ub, KG g, int D, const int64_t* __restrict__ offs,
                           uint64_t* __restrict__ out, int64_t cap) {
-  constexpr int NO = Nofs<DIM>::value;
-  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_ub) return;
-  const int64_t n = ctl[CTL_N];
-  if (i >= n || bal_nS(ctl, cap) == 0 || g.depth(k[i]) != D) return;
-  int64_t o = offs[i];
-  for (int oo = 0; oo < NO; ++oo) {
-    uint32_t N[3];
-    int dA;
-    if (!bal_query<DIM>(k, n, g, D, i, oo, N, &dA)) continue;
-    uint64_t rawN = interleave<DIM>(N);
-    for (int l = dA + 1; l <= D - 1; ++l) {
-      uint64_t span = vol_raw<DIM>(g, l - 1);
-      uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
-      for (int c = 0; c < (1 << DIM); ++c) out[o++] = child_key<DIM>(g, anc, c);
-    }
+  constexpr int LPL = BalLanes<DIM>::value;
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = gt / LPL;
+  const int o = int(gt % LPL);
+  const int64_t n = bal_nS(ctl, cap) > 0 ? ctl[CTL_N] : 0;
+  uint32_t N[3];
+  int dA = 0;
+  const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA) : 0;
+  // exclusive prefix of the counts among this leaf's lanes
+  int incl = c;
+#pragma unroll
+  for (int w = 1; w < LPL; w <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, w, LPL);
+    if (o >= w) incl += y;
+  }
+  if (c == 0) return;
+  int64_t q = offs[i] + (incl - c);
+  const uint64_t rawN = interleave<DIM>(N);
+  for (int l = dA + 1; l <= D - 1; ++l) {
+    const uint64_t span = vol_raw<DIM>(g, l - 1);
+    const uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
+    for (int ch = 0; ch < (1 << DIM); ++ch) out[q++] = child_key<DIM>(g, anc, ch);
   }
 }
 
 // Sort of the generated octants (at most SMALL_SORT_MAX) inside one block: bitonic network over a
 // power-of-two padded array in shared memory (padding = all-ones keys, which sort last and are
 // not written back).  Exchanges closer than 32 elements stay inside one warp and need only a
-// warp barrier.  Also the capacity check of the pass: an oversized pass is recorded, not sorted.
+// warp barrier.  Up to one key per thread, a rank sort is used instead (one pass over the keys).
+// Also the capacity check of the pass: an oversized pass is recorded, not sorted.
 constexpr int SMALL_SORT_MAX = 4096;
 __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t* __restrict__ ctl,
                                                      int64_t cap, int D) {
@@ -211,6 +231,22 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys
     return;
   }
   if (n == 0) return;
+  if (n <= int64_t(blockDim.x)) {
+    // rank sort: each key's position is the number of smaller keys plus the equal keys before it
+    const int t = threadIdx.x;
+    uint64_t mine = 0;
+    if (t < n) mine = sk[t] = keys[t];
+    __syncthreads();
+    if (t < n) {
+      int r = 0;
+      for (int j = 0; j < n; ++j) {
+        const uint64_t o = sk[j];
+        r += (o < mine) || (o == mine && j < t);
+      }
+      keys[r] = mine;
+    }
+    return;
+  }
   int P = 1;
   while (P < n) P <<= 1;
   for (int i = threadIdx.x; i < P; i += blockDim.x) sk[i] = i < n ? keys[i] : ~0ull;
@@ -618,7 +654,7 @@ static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<ui
   const int64_t G_ub = exact_G >= 0 ? exact_G : cap;
   FR_TRY(gen.ensure(A, size_t(G_ub)));
   FR_TRY(out.ensure(A, size_t(n_ub + G_ub)));
-  DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
+  DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n_ub * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
   FR_LAUNCH_CHECK(err);
   if (exact_G < 0 || exact_G <= SMALL_SORT_MAX) {
     k_sort_small<<<1, 1024, 0, s>>>(gen.p, d_ctl, cap, D);
@@ -661,7 +697,7 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, cnt)));
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n_ub * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
     if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + CTL_G, S, s, err))) break;
@@ -695,7 +731,7 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(nb), TB, 0, s>>>(keys.p, d_ctl, nb, g, D, cnt)));
+    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(nb * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, nb, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
     if ((rc = scan_counts(cnt, offs, nb, d_ctl + CTL_G, S, s, err))) break;

@@ -165,9 +165,37 @@ def experiment(steps: int = 120, snapshots: int = 30, log=print) -> dict:
     return res
 
 
+def bench_forward(n: int = 2_000_000, n_in: int = 55, reps: int = 10, seed: int = 1) -> dict:
+    """Times the tensor-core inference (fr_mlp_forward) on n seeded synthetic feature rows: CUDA
+    events around each call (which includes its status check and synchronisation)."""
+    import torch
+    npar = fr.mlp_param_count(n_in)
+    P = torch.from_numpy(((W.random_uniform(npar, seed) - 0.5) * 0.5).astype(np.float32)).cuda()
+    X = torch.from_numpy(((W.random_uniform(n * n_in, seed + 1) - 0.5) * 6).astype(np.float32))
+    X = X.reshape(n, n_in).cuda().to(torch.bfloat16)
+    fr.mlp_forward(P, X)
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fr.mlp_forward(P, X)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms)) * 1e-3
+    macs = n_in * 64 + 2 * 64 * 64 + 64 * 3
+    return dict(rows=n, in_dim=n_in, ms=t * 1e3, tflops=2.0 * macs * n / t / 1e12,
+                gbs=n * (2 * n_in + 12 + 1) / t / 1e9)
+
+
 if __name__ == "__main__":
     import json
     import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "--bench-forward":
+        n = int(sys.argv[2]) if len(sys.argv) > 2 else 2_000_000
+        n_in = int(sys.argv[3]) if len(sys.argv) > 3 else 55
+        print(json.dumps(bench_forward(n, n_in)))
+        sys.exit(0)
     out = experiment()
     print(json.dumps(out))
     if len(sys.argv) > 1:
