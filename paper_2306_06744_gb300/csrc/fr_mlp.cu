@@ -568,15 +568,22 @@ int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float
   int dev = 0;
   FR_CUDA(err, cudaGetDevice(&dev));
   const int smem = tc_plan(in).bytes;
-  static int sms = 0;
+  static int sms = 0, smem_sm = 0, resv = 0, regs = 0;
   if (sms == 0) {
-    FR_CUDA(err, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FR_CUDA(err, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    FR_CUDA(err, cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, dev));
     FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    cudaFuncAttributes fa{};
+    FR_CUDA(err, cudaFuncGetAttributes(&fa, k_mlp_forward_tc));
+    regs = fa.numRegs > 0 ? fa.numRegs : 255;
+    FR_CUDA(err, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
   FR_CUDA(err, cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  int per = 0;
-  FR_CUDA(err, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mlp_forward_tc, TC_ROWS, smem));
-  // every resident block holds TC_TMEM_COLS of the SM's 512 tensor-memory columns
+  // resident blocks per SM: shared memory, registers, and the SM's 512 tensor-memory columns of
+  // which every block holds TC_TMEM_COLS
+  int per = smem_sm / (smem + resv);
+  const int by_regs = 65536 / (regs * TC_ROWS);
+  if (per > by_regs) per = by_regs;
   if (per > 512 / TC_TMEM_COLS) per = 512 / TC_TMEM_COLS;
   const int64_t cap = int64_t(sms) * (per > 0 ? per : 1);
   const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
