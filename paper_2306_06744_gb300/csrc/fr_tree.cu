@@ -218,9 +218,9 @@ __global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restr
 // Sort of the generated octants (at most SMALL_SORT_MAX) inside one block: bitonic network over a
 // power-of-two padded array in shared memory (padding = all-ones keys, which sort last and are
 // not written back).  Exchanges closer than 32 elements stay inside one warp and need only a
-// warp barrier.  Up to one key per thread, a rank sort is used instead (one pass over the keys).
+// warp barrier.  Up to RANK_SORT_MAX keys a rank sort is used instead (one pass over the keys).
 // Also the capacity check of the pass: an oversized pass is recorded, not sorted.
-constexpr int SMALL_SORT_MAX = 4096;
+constexpr int SMALL_SORT_MAX = 4096, RANK_SORT_MAX = 256;
 __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t* __restrict__ ctl,
                                                      int64_t cap, int D) {
   __shared__ uint64_t sk[SMALL_SORT_MAX];
@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys
     return;
   }
   if (n == 0) return;
-  if (n <= int64_t(blockDim.x)) {
+  if (n <= RANK_SORT_MAX) {
     // rank sort: each key's position is the number of smaller keys plus the equal keys before it
+    // (n^2 comparisons on one SM: cheaper than the network's log^2 barriers only for small n)
     const int t = threadIdx.x;
     uint64_t mine = 0;
     if (t < n) mine = sk[t] = keys[t];
