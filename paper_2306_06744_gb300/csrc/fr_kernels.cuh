@@ -143,6 +143,31 @@ __device__ __forceinline__ ff cst<ff>(double x) {
   return ff_from_double(x);
 }
 
+// Programmatic dependent launch of the time-step kernels: each interface and element kernel is
+// launched so that its blocks may be scheduled while its predecessor in the stream drains.  Every
+// such kernel first waits (in hardware) until the predecessor grid has completed and its writes
+// are visible, and only then lets its own dependents launch, so a kernel never overlaps anything
+// but the tail of its immediate predecessor, and all its reads and writes come after that wait.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class Kern, class... Args>
+cudaError_t launch_dependent(Kern kernel, unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
 template <int DIM, int NP, class T>
 __global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid_constant__ OpsT<T> ops,
@@ -185,6 +210,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   T* fcomm = static_cast<T*>(A.fcomm);
   const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
   const int tid = threadIdx.x;
+  pdl_wait_then_release();
   if (int64_t(blockIdx.x) >= A.nb_hang) {
     int64_t idx = (int64_t(blockIdx.x) - A.nb_hang) * BT + tid;
     int64_t face = idx / NF;
@@ -314,6 +340,7 @@ __global__ void __launch_bounds__(128) k_stage_t(StageArgs A, const __grid_const
   const int tid = threadIdx.x;
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
   const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
+  pdl_wait_then_release();
   for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
   for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
@@ -464,7 +491,9 @@ int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t 
                    const int NF = DD == 2 ? NN : NN * NN;
                    A.nb_conf = (A.n_conf * NF + FC::T - 1) / FC::T;
                    A.nb_hang = (A.n_hang + FC::FPB - 1) / FC::FPB;
-                   k_faces_t<DD, NN, T><<<unsigned(A.nb_conf + A.nb_hang), FC::T, 0, s>>>(A, ops);
+                   if (launch_dependent(k_faces_t<DD, NN, T>, unsigned(A.nb_conf + A.nb_hang), FC::T, s, A, ops) !=
+                       cudaSuccess)
+                     return set_error(err, FR_ECUDA, "interface kernel launch");
                  }));
   FR_LAUNCH_CHECK(err);
   return 0;
@@ -477,7 +506,8 @@ int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaS
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    unsigned nb = unsigned((A.M + SS::EPB - 1) / SS::EPB);
-                   k_stage_t<DD, NN, T><<<nb, 128, 0, s>>>(A, ops);
+                   if (launch_dependent(k_stage_t<DD, NN, T>, nb, 128, s, A, ops) != cudaSuccess)
+                     return set_error(err, FR_ECUDA, "element kernel launch");
                  }));
   FR_LAUNCH_CHECK(err);
   return 0;
