@@ -68,6 +68,7 @@ inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); 
 template <int DIM>
 __global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M_ub, const int64_t* __restrict__ d_M,
                              int64_t* __restrict__ c) {
+  pdl_wait_then_release();
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M_ub) return;
   if (d_M && e >= *d_M) {
@@ -88,6 +89,7 @@ template <int DIM>
 __global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
                              int64_t M_ub, const int64_t* __restrict__ d_M, const int64_t* __restrict__ off,
                              int32_t* __restrict__ conf, int32_t* __restrict__ hang, int32_t* __restrict__ hcon) {
+  pdl_wait_then_release();
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M_ub || (d_M && e >= *d_M)) return;
   int64_t a = off[e] & 0xFFFFFFFFll, b = off[e] >> 32;
@@ -143,9 +145,9 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   FR_CUDA(err, cudaMemsetAsync(m->contrib.p, 0xff, size_t(S) * 16, s));
   FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
   if (m->dim == 2)
-    k_face_count<2><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, n_ub, d_n, cnt);
+    launch_dependent(k_face_count<2>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
   else
-    k_face_count<3><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, n_ub, d_n, cnt);
+    launch_dependent(k_face_count<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
   FR_LAUNCH_CHECK(err);
   FR_TRY(scan_counts64(cnt, off, n_ub, d_faces, Sc, s, err));
   // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
@@ -154,9 +156,11 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   FR_TRY(m->hang.ensure(m->A, size_t(n_ub) * m->nfc));
   FR_TRY(hcon.ensure(m->A, size_t(n_ub) * m->nfc * 4));
   if (m->dim == 2)
-    k_face_write<2><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, m->contrib.p, n_ub, d_n, off, m->conf.p, m->hang.p, hcon.p);
+    launch_dependent(k_face_write<2>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p),
+                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, static_cast<const int64_t*>(off), m->conf.p, m->hang.p, hcon.p);
   else
-    k_face_write<3><<<nblk(n_ub), TB, 0, s>>>(m->ftype.p, m->contrib.p, n_ub, d_n, off, m->conf.p, m->hang.p, hcon.p);
+    launch_dependent(k_face_write<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p),
+                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, static_cast<const int64_t*>(off), m->conf.p, m->hang.p, hcon.p);
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -45,6 +45,32 @@ int64_t& launch_counter();
     FR_CUDA(err, cudaGetLastError());   \
   } while (0)
 
+// Programmatic dependent launch: the time-step and adaptation kernels are launched so that their
+// blocks may be scheduled while the predecessor in the stream drains.  Every such kernel first
+// waits (in hardware) until the predecessor grid has completed and its writes are visible, and
+// only then lets its own dependents launch, so a kernel never overlaps anything but the tail of
+// its immediate predecessor, and all its reads and writes come after that wait.  (Without the
+// launch attribute the wait returns at once.)
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class Kern, class... Args>
+cudaError_t launch_dependent(Kern kernel, unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Morton IDs (Sec. 2.2, Algorithm 1).  Bits are interleaved with the "magic number" bit spread
 // the paper mentions: spreading one coordinate's bits to every dim-th position by masked shifts.

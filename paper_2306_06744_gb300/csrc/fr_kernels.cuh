@@ -143,35 +143,11 @@ __device__ __forceinline__ ff cst<ff>(double x) {
   return ff_from_double(x);
 }
 
-// Programmatic dependent launch of the time-step kernels: each interface and element kernel is
-// launched so that its blocks may be scheduled while its predecessor in the stream drains.  Every
-// such kernel first waits (in hardware) until the predecessor grid has completed and its writes
-// are visible, and only then lets its own dependents launch, so a kernel never overlaps anything
-// but the tail of its immediate predecessor, and all its reads and writes come after that wait.
-__device__ __forceinline__ void pdl_wait_then_release() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
-template <class Kern, class... Args>
-cudaError_t launch_dependent(Kern kernel, unsigned grid, unsigned block, cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 // traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
 template <int DIM, int NP, class T>
 __global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid_constant__ OpsT<T> ops,
                            T* __restrict__ tr) {
+  pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= M * S::EF) return;
@@ -477,7 +453,7 @@ int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps&
   OpsT<T> ops = make_ops_t<T>(o);
   int64_t Tn = M * 2 * dim * (dim + 2) * ipow_k(p + 1, dim - 1);
   unsigned nb = unsigned((Tn + 127) / 128);
-  FR_NP_DISPATCH(dim, p, (k_traces_t<DD, NN, T><<<nb, 128, 0, s>>>(u, M, ops, static_cast<T*>(tr))));
+  FR_NP_DISPATCH(dim, p, (launch_dependent(k_traces_t<DD, NN, T>, nb, 128, s, u, M, ops, static_cast<T*>(tr))));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -110,6 +110,7 @@ template <class TIn>
 __global__ void __launch_bounds__(SCAN_T) k_scan_tile(const TIn* __restrict__ in,
                                                       int64_t* __restrict__ out, int64_t n,
                                                       int64_t* __restrict__ sums) {
+  pdl_wait_then_release();
   __shared__ int64_t s_warp[SCAN_T / 32];
   __shared__ TIn s_in[SCAN_TILE];
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_tile(const TIn* __restrict__ in
 }
 
 __global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
+  pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i < n) out[i] += offs[i / SCAN_TILE];
 }
@@ -175,6 +177,7 @@ constexpr int64_t SCAN_PREFIX_MAX = 256;
 __global__ void __launch_bounds__(256) k_scan_add_prefix(int64_t* __restrict__ out, int64_t n,
                                                          const int64_t* __restrict__ sums, int64_t nb,
                                                          int64_t* __restrict__ total) {
+  pdl_wait_then_release();
   __shared__ int64_t red[256];
   const int t = threadIdx.x;
   const int64_t i0 = int64_t(blockIdx.x) * 256;
@@ -212,16 +215,17 @@ static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_tota
   }
   int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
   if (nb == 1) {
-    k_scan_tile<TIn><<<1, SCAN_T, 0, s>>>(d_in, d_out, n, d_total);
+    launch_dependent(k_scan_tile<TIn>, 1, SCAN_T, s, d_in, d_out, n, d_total);
     FR_LAUNCH_CHECK(err);
     return 0;
   }
   if (nb <= SCAN_PREFIX_MAX) {
     int64_t* sums1 = S.get<int64_t>(nb);
     if (!sums1) return set_error(err, FR_ENOMEM, "scan scratch");
-    k_scan_tile<TIn><<<unsigned(nb), SCAN_T, 0, s>>>(d_in, d_out, n, sums1);
+    launch_dependent(k_scan_tile<TIn>, unsigned(nb), SCAN_T, s, d_in, d_out, n, sums1);
     FR_LAUNCH_CHECK(err);
-    k_scan_add_prefix<<<unsigned((n + 255) / 256), 256, 0, s>>>(d_out, n, sums1, nb, d_total);
+    launch_dependent(k_scan_add_prefix, unsigned((n + 255) / 256), 256, s, d_out, n,
+                     static_cast<const int64_t*>(sums1), nb, d_total);
     FR_LAUNCH_CHECK(err);
     return 0;
   }

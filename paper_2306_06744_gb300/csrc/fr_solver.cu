@@ -209,6 +209,7 @@ __global__ void k_indicator(const uint64_t* __restrict__ keys, int64_t M, KG g, 
                             double th_r, double th_c, double t, const __grid_constant__ DevProblem P,
                             const __grid_constant__ DevOps ops, const double* __restrict__ u,
                             int8_t* __restrict__ flags, double* __restrict__ eta) {
+  pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M) return;
@@ -264,6 +265,7 @@ __global__ void k_transfer(KG g, const uint64_t* __restrict__ old_keys,
                            const int8_t* __restrict__ tag, int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
                            const __grid_constant__ DevOps ops, const double* __restrict__ uo,
                            double* __restrict__ un) {
+  pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= Mn_ub * S::N || (d_Mn && idx >= *d_Mn * S::N)) return;
@@ -483,7 +485,8 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
                      const DevOps& ops, const double* u, int8_t* flags, double* eta,
                      cudaStream_t s, Err* err) {
   if (M <= 0) return 0;
-  FR_DISPATCH(dim, p, (k_indicator<DD, NN><<<nb_of(M, 128), 128, 0, s>>>(keys, M, g, mode, th_r, th_c, t, P, ops, u, flags, eta)));
+  FR_DISPATCH(dim, p, (launch_dependent(k_indicator<DD, NN>, nb_of(M, 128), 128, s, keys, M, g, mode, th_r, th_c, t, P,
+                                        ops, u, flags, eta)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
@@ -493,7 +496,8 @@ int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const
                     const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err) {
   if (M_new <= 0) return 0;
   int64_t T = M_new * ipow(p + 1, dim);
-  FR_DISPATCH(dim, p, (k_transfer<DD, NN><<<nb_of(T, 128), 128, 0, s>>>(g, old_keys, new_keys, src, tag, M_new, d_M_new, ops, u_old, u_new)));
+  FR_DISPATCH(dim, p, (launch_dependent(k_transfer<DD, NN>, nb_of(T, 128), 128, s, g, old_keys, new_keys, src, tag, M_new,
+                                        d_M_new, ops, u_old, u_new)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -67,6 +67,7 @@ template <int DIM>
 __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __restrict__ flags,
                              int64_t n, KG g, int Dbase, int8_t* __restrict__ act,
                              int32_t* __restrict__ cnt) {
+  pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   constexpr int NC = 1 << DIM;
@@ -95,6 +96,7 @@ template <int DIM>
 __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __restrict__ act,
                              const int64_t* __restrict__ offs, int64_t n, KG g,
                              uint64_t* __restrict__ out, unsigned long long* stats) {
+  pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t key = k[i];
@@ -173,6 +175,7 @@ __device__ __forceinline__ int bal_lane(const uint64_t* __restrict__ k, int64_t 
 template <int DIM>
 __global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                             int64_t n_ub, KG g, int D, int32_t* __restrict__ cnt) {
+  pdl_wait_then_release();
   constexpr int LPL = BalLanes<DIM>::value;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = gt / LPL;
@@ -190,6 +193,7 @@ template <int DIM>
 __global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                           int64_t n_ub, KG g, int D, const int64_t* __restrict__ offs,
                           uint64_t* __restrict__ out, int64_t cap) {
+  pdl_wait_then_release();
   constexpr int LPL = BalLanes<DIM>::value;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = gt / LPL;
@@ -223,6 +227,7 @@ __global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restr
 constexpr int SMALL_SORT_MAX = 4096, RANK_SORT_MAX = 256;
 __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys, int64_t* __restrict__ ctl,
                                                      int64_t cap, int D) {
+  pdl_wait_then_release();
   __shared__ uint64_t sk[SMALL_SORT_MAX];
   if (ctl[CTL_OVER] != 0) return;
   const int64_t n = ctl[CTL_G];
@@ -290,6 +295,7 @@ template <int DIM>
 __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl,
                               int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
                               int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
+  pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
   const int64_t nS = bal_nS(ctl, cap);
@@ -316,6 +322,7 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
                               int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
                               const int32_t* __restrict__ cnt, const int64_t* __restrict__ lo,
                               const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
+  pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
   const int c = cnt[i];
@@ -335,6 +342,7 @@ template <int DIM>
 __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64_t* __restrict__ nw,
                       int64_t nn_ub, const int64_t* __restrict__ d_nn, KG g, int32_t* __restrict__ src,
                       int8_t* __restrict__ tag, int32_t* bad) {
+  pdl_wait_then_release();
   int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= nn_ub || (d_nn && j >= *d_nn)) return;
   uint64_t key = nw[j];
@@ -366,6 +374,7 @@ template <int DIM>
 __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64_t* __restrict__ d_n, KG g,
                        int32_t* __restrict__ nbr, int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
                        int32_t* __restrict__ contrib, int32_t* bad) {
+  pdl_wait_then_release();
   constexpr int NFC = 2 * DIM;
   int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= n_ub * NFC) return;
@@ -626,10 +635,10 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   // the leaf count stays on the device for the balance passes
   FR_TRY(out.ensure(A, size_t(n) << dim));
   FR_CUDA(err, cudaMemsetAsync(d_ctl, 0, CTL_SLOTS * sizeof(int64_t), s));
-  DIM_DISPATCH(dim, (k_edit_count<D_><<<nblk(n), TB, 0, s>>>(d_keys, d_flags, n, g, Dbase, act, cnt)));
+  DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt)));
   FR_LAUNCH_CHECK(err);
   FR_TRY(scan_counts(cnt, offs, n, d_ctl + CTL_N, S, s, err));
-  DIM_DISPATCH(dim, (k_edit_write<D_><<<nblk(n), TB, 0, s>>>(d_keys, act, offs, n, g, out.p,
+  DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, offs, n, g, out.p,
                                                                reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF))));
   FR_LAUNCH_CHECK(err);
   return 0;
@@ -655,10 +664,10 @@ static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<ui
   const int64_t G_ub = exact_G >= 0 ? exact_G : cap;
   FR_TRY(gen.ensure(A, size_t(G_ub)));
   FR_TRY(out.ensure(A, size_t(n_ub + G_ub)));
-  DIM_DISPATCH(dim, (k_bal_gen<D_><<<nblk(n_ub * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
+  DIM_DISPATCH(dim, (launch_dependent(k_bal_gen<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
   FR_LAUNCH_CHECK(err);
   if (exact_G < 0 || exact_G <= SMALL_SORT_MAX) {
-    k_sort_small<<<1, 1024, 0, s>>>(gen.p, d_ctl, cap, D);
+    launch_dependent(k_sort_small, 1, 1024, s, gen.p, d_ctl, cap, D);
     FR_LAUNCH_CHECK(err);
   } else {
     FR_TRY(tmp.ensure(A, size_t(exact_G)));
@@ -668,11 +677,11 @@ static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<ui
   int64_t* lo = S.get<int64_t>(n_ub);
   int64_t* offs2 = S.get<int64_t>(n_ub);
   if (!cnt2 || !lo || !offs2) return set_error(err, FR_ENOMEM, "balance merge scratch");
-  DIM_DISPATCH(dim, (k_merge_count<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo)));
+  DIM_DISPATCH(dim, (launch_dependent(k_merge_count<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo)));
   FR_LAUNCH_CHECK(err);
   // the merged tree has at most n + G leaves; its count replaces ctl[CTL_N] on the device
   FR_TRY(scan_counts(cnt2, offs2, n_ub, d_ctl + CTL_N, S, s, err));
-  DIM_DISPATCH(dim, (k_merge_write<D_><<<nblk(n_ub), TB, 0, s>>>(keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo, offs2, out.p)));
+  DIM_DISPATCH(dim, (launch_dependent(k_merge_write<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo, offs2, out.p)));
   FR_LAUNCH_CHECK(err);
   Buf<uint64_t> t = keys;  // the merged tree becomes the tree
   keys = out;
@@ -698,7 +707,7 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(n_ub * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, n_ub, g, D, cnt)));
+    DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
     if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + CTL_G, S, s, err))) break;
@@ -732,7 +741,7 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (k_bal_count<D_><<<nblk(nb * BalLanes<D_>::value), TB, 0, s>>>(keys.p, d_ctl, nb, g, D, cnt)));
+    DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
     if ((rc = scan_counts(cnt, offs, nb, d_ctl + CTL_G, S, s, err))) break;
@@ -750,7 +759,7 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
              int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,
              cudaStream_t s, Err* err) {
   if (n_new <= 0) return 0;
-  DIM_DISPATCH(dim, (k_map<D_><<<nblk(n_new), TB, 0, s>>>(d_old, n_old, d_new, n_new, d_n_new, g, d_src, d_tag, d_bad)));
+  DIM_DISPATCH(dim, (launch_dependent(k_map<D_>, nblk(n_new), TB, s, d_old, n_old, d_new, n_new, d_n_new, g, d_src, d_tag, d_bad)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
@@ -759,7 +768,7 @@ int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int
               Err* err) {
   if (n <= 0) return 0;
   int64_t T = n * 2 * dim;
-  DIM_DISPATCH(dim, (k_conn<D_><<<nblk(T), TB, 0, s>>>(d_keys, n, d_n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
+  DIM_DISPATCH(dim, (launch_dependent(k_conn<D_>, nblk(T), TB, s, d_keys, n, d_n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
