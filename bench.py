@@ -308,14 +308,18 @@ def main():
     # end-to-end through the public API with host buffers
     e2e = None
     if args.e2e_steps > 0:
-        keys_h = torch.empty(0)
+        # pinned host buffers for the step's inputs and its result, sized with room for growth
+        cap = 2 * mesh.M
+        kin = torch.empty(cap, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        uin = torch.empty(cap * nv * N, dtype=torch.float64).pin_memory().numpy()
+        kout = torch.empty(cap, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+        uout = torch.empty(cap * nv * N, dtype=torch.float64).pin_memory().numpy()
+        keys_h = None
         dof_e, t_e, bi, bo = 0, 0.0, 0, 0
         for k in range(args.e2e_steps + 1):
-            keys = mesh.leaves()
-            u = mesh.state()
-            kp = torch.from_numpy(keys.view(np.int64)).pin_memory()
-            up = torch.from_numpy(u).pin_memory()
-            kn, un_ = kp.numpy().view(np.uint64), up.numpy()
+            Mk = mesh.M
+            kn = mesh.leaves(out=kin)
+            un_ = mesh.state(out=uin)
             torch.cuda.synchronize()
             flush.fill_(float(k))
             torch.cuda.synchronize()
@@ -324,9 +328,10 @@ def main():
             M0 = mesh.M
             mesh.step(ae)
             mesh.adapt()
-            k2 = mesh.leaves()
-            u2 = mesh.state()
+            k2 = mesh.leaves(out=kout)
+            u2 = mesh.state(out=uout)
             b = time.perf_counter()
+            assert Mk == M0 and mesh.M <= cap
             if k == 0:
                 continue  # first pass warms the pinned-buffer path
             dof_e += ae * M0 * N * nv

@@ -699,33 +699,53 @@ int fr_get_state(fr_mesh* m, double* host_u, int64_t cap) {
 int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double* host_u) {
   if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
   if (M <= 0 || !host_keys || !host_u) return set_error(&m->err, FR_EINVAL, "bad arguments");
+  Err* err = &m->err;
+  cudaStream_t s = m->stream;
+  // keys and state are copied in, the keys validated and the connectivity built, with one
+  // synchronisation; the state lands in the stage buffer, so the current one survives a rejection
   Buf<uint64_t> nk;
+  Buf<int32_t> hcon;
+  Scratch Sc(&m->A);
+  int32_t* bad = Sc.get<int32_t>(3);  // [0] 2:1 violation, [1] (mapping, unused here), [2] invalid tree
+  int64_t* tot = Sc.get<int64_t>(1);
+  if (!bad || !tot) return set_error(err, FR_ENOMEM, "set_state scratch");
   FR_TRY(nk.ensure(m->A, M));
-  FR_TRY(host_copy(&m->err, nk.p, host_keys, size_t(M) * 8, cudaMemcpyHostToDevice, m->stream));
-  bool ok = false;
-  int rc = tree_validate(m->dim, m->g, nk.p, M, m->cfg.Dbase, m->cfg.Dmax, &ok, m->A, m->stream, &m->err);
-  if (!rc && !ok) rc = set_error(&m->err, FR_EINVAL, "keys are not a complete sorted linear tree in [Dbase, Dmax]");
+  FR_TRY(m->w.ensure(m->A, size_t(M) * m->EU));
+  int rc = 0;
+  if (cudaMemcpyAsync(nk.p, host_keys, size_t(M) * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(m->w.p, host_u, size_t(M) * m->EU * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemsetAsync(bad, 0, 12, s) != cudaSuccess)
+    rc = set_error(err, FR_ECUDA, "set_state copies");
+  if (!rc) rc = tree_validate_async(m->dim, m->g, nk.p, M, m->cfg.Dbase, m->cfg.Dmax, bad + 2, s, err);
+  if (!rc) rc = conn_issue(m, nk.p, M, nullptr, tot, bad, hcon);
+  int64_t h = 0;
+  int32_t hb[3] = {0, 0, 0};
+  if (!rc && (cudaMemcpyAsync(&h, tot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaMemcpyAsync(hb, bad, 12, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+    rc = set_error(err, FR_ECUDA, "set_state read");
+  if (!rc && hb[2]) rc = set_error(err, FR_EINVAL, "keys are not a complete sorted linear tree in [Dbase, Dmax]");
+  if (!rc && hb[0]) rc = set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
   if (rc) {
+    // the tables were overwritten for the rejected keys: rebuild them for the current tree
     nk.release(m->A);
+    hcon.release(m->A);
+    Err keep = *err;
+    rebuild_conn(m);
+    *err = keep;
     return rc;
   }
   Buf<uint64_t> old = m->keys;
-  int64_t oldM = m->M;
   m->keys = nk;
-  m->M = M;
-  rc = ensure_state(m, M);
-  if (!rc) rc = rebuild_conn(m);
-  if (rc) {
-    // restore the previous tree
-    m->keys = old;
-    m->M = oldM;
-    nk.release(m->A);
-    int rc2 = rebuild_conn(m);
-    (void)rc2;
-    return rc;
-  }
   old.release(m->A);
-  FR_TRY(host_copy(&m->err, m->u.p, host_u, size_t(M) * m->EU * 8, cudaMemcpyHostToDevice, m->stream));
+  m->M = M;
+  Buf<double> ou = m->u;  // the stage buffer holding the new state becomes the state
+  m->u = m->w;
+  m->w = ou;
+  rc = conn_finish(m, h, hb, hcon);
+  hcon.release(m->A);
+  FR_TRY(rc);
+  FR_TRY(ensure_state(m, M));
   return refresh_traces(m);
 }
 

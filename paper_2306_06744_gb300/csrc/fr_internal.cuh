@@ -319,6 +319,9 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
               Err* err);
+// sets *d_bad (not cleared here) unless keys are a complete sorted linear tree with depths in [Dlo, Dhi]
+int tree_validate_async(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
+                        int32_t* d_bad, cudaStream_t s, Err* err);
 // checks that keys are a complete sorted linear tree with depths in [Dlo, Dhi]
 int tree_validate(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
                   bool* ok, Alloc& A, cudaStream_t s, Err* err);

@@ -773,6 +773,14 @@ int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int
   return 0;
 }
 
+int tree_validate_async(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
+                        int32_t* d_bad, cudaStream_t s, Err* err) {
+  if (n <= 0) return 0;
+  DIM_DISPATCH(dim, (k_validate<D_><<<nblk(n), TB, 0, s>>>(d_keys, n, g, Dlo, Dhi, d_bad)));
+  FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
 int tree_validate(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
                   bool* ok, Alloc& A, cudaStream_t s, Err* err) {
   Scratch S(&A);

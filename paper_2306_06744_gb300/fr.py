@@ -161,6 +161,14 @@ def _stream_handle(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
+def _host_out(out, n, dtype):
+    if out is None:
+        return np.empty(n, dtype=dtype)
+    if out.dtype != dtype or not out.flags["C_CONTIGUOUS"] or out.size < n:
+        raise ValueError("out must be a contiguous %s array of at least %d entries" % (np.dtype(dtype), n))
+    return out.reshape(-1)[:n]
+
+
 def make_config(cfg: dict):
     vort = np.ascontiguousarray(np.asarray(cfg["vort"], dtype=np.float64).reshape(-1, 4))
     c = FRConfig(dim=cfg["dim"], p=cfg["p"], L=cfg["L"], Dbase=cfg["Dbase"], Dmax=cfg["Dmax"],
@@ -293,18 +301,22 @@ class Mesh:
         return dict(t=o.t, l2_rho=o.l2_rho, integral=list(o.integral)[: self.nv],
                     min_rho=o.min_rho, min_p=o.min_p, M=o.M)
 
-    def leaves(self):
+    def leaves(self, out=None):
+        """Morton keys of the leaves (uint64[M]).  `out`: a contiguous uint64 host array of at least
+        M entries to fill (e.g. a view of pinned memory); the result is then a view of it."""
         M = self.M
-        k = np.zeros(M, dtype=np.uint64)
+        k = _host_out(out, M, np.uint64)
         m = C.c_int64()
         self._ck(load().fr_get_leaves(self.h, _np_ptr(k), M, C.byref(m)))
         return k
 
-    def state(self):
+    def state(self, out=None):
+        """Conserved variables u[M][nv][N] (FP64).  `out`: a contiguous float64 host array of at
+        least M*nv*N entries to fill; the result is then a view of it."""
         M = self.M
-        u = np.zeros((M, self.nv, self.N))
+        u = _host_out(out, M * self.nv * self.N, np.float64)
         self._ck(load().fr_get_state(self.h, _np_ptr(u), u.size))
-        return u
+        return u.reshape(M, self.nv, self.N)
 
     def set_state(self, keys, u):
         keys = np.ascontiguousarray(keys, dtype=np.uint64)

@@ -165,7 +165,33 @@ def test_set_state_rejects_bad_tree():
     with pytest.raises(fr.FRError) as e:
         g.set_state(keys[1:], u[1:])  # incomplete
     assert e.value.code == fr.FR_EINVAL
-    assert np.array_equal(g.leaves(), keys)  # unchanged
+    # complete but not 2:1 balanced: the first base cell refined twice in its first corner
+    dim, Dmax = cfg["dim"], cfg["Dmax"]
+    b = O.morton_decode(dim, Dmax, keys)
+    d0 = int(b[0, 0])
+    boxes = [tuple(x) for x in b[1:]]
+    corner = (d0, 0, 0, 0)
+    q = [corner]
+    for _ in range(2):
+        c = q.pop(0)
+        h = 1 << (Dmax - c[0] - 1)
+        kids = [(c[0] + 1, c[1] + (k & 1) * h, c[2] + (k >> 1) * h, 0) for k in range(4)]
+        q.append(kids[0])
+        boxes += kids[1:]
+    boxes += q
+    bad = np.sort(O.morton_encode(dim, Dmax, np.array(boxes)))
+    assert len(O.balance(dim, Dmax, bad)) > len(bad)
+    ub = np.ones((len(bad), g.nv, g.N))
+    with pytest.raises(fr.FRError) as e:
+        g.set_state(bad, ub)
+    assert e.value.code == fr.FR_EINVAL
+    # the mesh is unchanged and still steps exactly like a fresh copy of it
+    assert np.array_equal(g.leaves(), keys)
+    assert np.array_equal(g.state(), u)
+    h = fr.Mesh(cfg)
+    g.step(5)
+    h.step(5)
+    assert np.array_equal(g.state(), h.state())
 
 
 def test_init_rejects_bad_config():
