@@ -59,7 +59,11 @@ struct Sz {
   static constexpr int NSUB = 1 << (DIM - 1);
   static constexpr int EU = NV * N;         // values per element state
   static constexpr int EF = NFC * NV * NF;  // values per element face data
-  static constexpr int EPB = (128 / N) > 0 ? (128 / N) : 1;  // elements per 128-thread block
+  // elements per block of the element kernel, one thread per point: 128/N elements, except for
+  // N = 27 (3D, p = 2) where 4 elements would leave 20 of 128 threads idle: 7 elements fill
+  // 189 of 192 (the shared-memory stage stays under 48 KB)
+  static constexpr int EPB = N == 27 ? 7 : ((128 / N) > 0 ? (128 / N) : 1);
+  static constexpr int BT = (EPB * N + 31) / 32 * 32;  // threads per block
 };
 
 // element point index of position j along `axis` on the line through face point q
@@ -302,7 +306,7 @@ struct RkT<ff> {
 // (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt), then
 // out = a*un + b*us + c*R (Eq. rk3), and (optionally) the traces of out.
 template <int DIM, int NP, class T>
-__global__ void __launch_bounds__(128) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
+__global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
   using S = Sz<DIM, NP>;
   using RT = typename RkT<T>::type;
   constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF;
@@ -482,7 +486,7 @@ int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaS
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    unsigned nb = unsigned((A.M + SS::EPB - 1) / SS::EPB);
-                   if (launch_dependent(k_stage_t<DD, NN, T>, nb, 128, s, A, ops) != cudaSuccess)
+                   if (launch_dependent(k_stage_t<DD, NN, T>, nb, SS::BT, s, A, ops) != cudaSuccess)
                      return set_error(err, FR_ECUDA, "element kernel launch");
                  }));
   FR_LAUNCH_CHECK(err);
