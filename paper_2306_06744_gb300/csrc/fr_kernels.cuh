@@ -172,11 +172,28 @@ __global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid
 // that they are not left running alone at the end of the grid.
 // block size of the interface kernel: 64 threads (more, smaller blocks spread one partial wave
 // evenly over the SMs) unless one hanging face needs more threads than that
+// faces per block (1..8, at most 512 threads) that leave the fewest idle lanes in whole warps
+constexpr int face_fpb(int per) {
+  int best = 1, bn = 0, bd = 1;
+  for (int f = 1; f <= 8 && f * per <= 512; ++f) {
+    const int n = f * per, d = (n + 31) / 32 * 32;
+    if (n * bd > bn * d) {
+      best = f;
+      bn = n;
+      bd = d;
+    }
+  }
+  return best;
+}
+
 template <int DIM, int NP>
 struct FaceCfg {
-  static constexpr int PER = (1 << (DIM - 1)) * (DIM == 2 ? NP : NP * NP);
-  static constexpr int T = PER > 64 ? 128 : 64;
-  static constexpr int FPB = T / PER;
+  static constexpr int PER = (1 << (DIM - 1)) * (DIM == 2 ? NP : NP * NP);  // threads per hanging face
+  static constexpr int T0 = PER > 64 ? 128 : 64;
+  static constexpr bool FULL = (T0 / PER) * PER * 10 >= T0 * 9;  // at most a tenth of T0 idle
+  // otherwise (3D p = 2: one 36-point face per 64 threads) as many faces as fill whole warps
+  static constexpr int FPB = FULL ? T0 / PER : face_fpb(PER);
+  static constexpr int T = FULL ? T0 : (FPB * PER + 31) / 32 * 32;
 };
 
 template <int DIM, int NP, class T>
