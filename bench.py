@@ -293,7 +293,7 @@ def main():
     value = world * dof_rank / t_tot
     norms = mesh.norms()
 
-    # element-kernel roofline (FP64: bound by the FP64 pipe, see DESIGN.md)
+    # element-kernel roofline (FP64: bound by the FP64 pipe)
     st_s = prof["stage_ms"] / 1e3
     stage_avg_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
     n_stage = 3 * ae * args.steps  # element (and interface) kernel launches in the timed region
