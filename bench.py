@@ -177,6 +177,20 @@ def run_reference(args):
     return 0
 
 
+def aggregate_ranks(units, seconds, device="cuda"):
+    """Whole-job throughput inputs over the ranks of a replica run: the units every rank
+    processed, summed, and the slowest rank's time (one rank: unchanged)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(seconds)
+    a = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    b = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(b, op=dist.ReduceOp.MAX)
+    return float(a.item()), float(b.item())
+
+
 def _kernel_source_hash():
     """Hash of the element-stage kernel's source text (the k_stage_t definition)."""
     import hashlib
@@ -285,12 +299,9 @@ def main():
     t_step = sum(a.elapsed_time(b) for a, b, _ in evs) / 1e3
     t_adapt = sum(b.elapsed_time(c) for _, b, c in evs) / 1e3
     t_tot = t_step + t_adapt
-    if world > 1:
-        tt = torch.tensor([t_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_tot = float(tt.item())
     dof_rank = sum(ae * m * N * nv for m in Ms)
-    value = world * dof_rank / t_tot
+    dof_all, t_tot = aggregate_ranks(dof_rank, t_tot)
+    value = dof_all / t_tot
     norms = mesh.norms()
 
     # element-kernel roofline (FP64: bound by the FP64 pipe)
@@ -357,7 +368,8 @@ def main():
             t_e += b - a
             bi += kn.nbytes + un_.nbytes
             bo += k2.nbytes + u2.nbytes
-        e2e = {"value": world * dof_e / t_e, "unit": UNIT,
+        dof_e, t_e = aggregate_ranks(dof_e, t_e)
+        e2e = {"value": dof_e / t_e, "unit": UNIT,
                "h2d_bytes_per_step": bi // args.e2e_steps, "d2h_bytes_per_step": bo // args.e2e_steps}
         del keys_h
 
@@ -390,7 +402,8 @@ def main():
             fs = sum(a.elapsed_time(b) for a, b, _ in fev) / 1e3
             fa = sum(b.elapsed_time(c) for _, b, c in fev) / 1e3
             fn = fm.norms()
-            forms[name] = {"value": world * sum(ae * m * N * nv for m in fMs) / (fs + fa),
+            fdof, ft = aggregate_ranks(sum(ae * m * N * nv for m in fMs), fs + fa)
+            forms[name] = {"value": fdof / ft,
                            "l2_rho": fn["l2_rho"], "time_to_solution_s": fs + fa,
                            "adaptation_pct": 100.0 * fa / (fs + fa), "M_final": fm.M,
                            "stage_kernel_avg_ms": fp["stage_ms"] / max(1, fp["stage_launches"]),
