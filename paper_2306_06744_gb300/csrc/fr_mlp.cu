@@ -18,6 +18,7 @@
 
 #include <cmath>
 
+#include "fr_arith.cuh"
 #include "fr_internal.cuh"
 #include "fr_mlp.cuh"
 #include "fr_tc.cuh"
@@ -58,16 +59,20 @@ __host__ __device__ inline Lay lay(int in) {
 }
 
 // features from the FP64 state: the conserved variables are interpolated from the element's own
-// points to the 3 Gauss-Legendre points per axis (I3 = 3 x n Lagrange matrix), where density and
-// pressure are taken
+// points to the 3 Gauss-Legendre points per axis (I3 = 3 x n Lagrange matrix, as double-word
+// constants), where density and pressure are taken
 struct I3Mat {
-  double m[3][NPMAX];
+  ff m[3][NPMAX];
 };
 
-// One thread per element.  The interpolation to the 3^dim sample points is sum-factorised (one
-// axis at a time: n^dim -> 3 n^(dim-1) -> ... -> 3^dim values per variable) in FP64; density is
-// kept per sample point, the squared momentum accumulated, and pressure formed when the energy
-// arrives.  In 3D the first two axes are done per z-slice, so only 3^2 n values stay live.
+// One thread per element, in double-word arithmetic (pairs of floats, ~48-bit significand, on
+// the FP32 pipes; the state converts from FP64 by integer operations): the features are relative
+// deviations of nearly equal values, which FP32 alone would swamp with rounding noise, while FP64
+// on GB300 runs at 1/58 of the FP32 rate.  The interpolation to the 3^dim sample points is
+// sum-factorised (one axis at a time: n^dim -> 3 n^(dim-1) -> ... -> 3^dim values per variable);
+// density is kept per sample point, the squared momentum accumulated, and pressure formed when
+// the energy arrives.  In 3D the first two axes are done per z-slice, so only 3^2 n values stay
+// live.
 template <int DIM, int NP>
 __global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, const uint64_t* __restrict__ keys,
                                                   int64_t M, KG g, int Dbase, double gamma,
@@ -79,24 +84,25 @@ __global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, 
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M) return;
   const double* q = u + e * NV * N;
-  double rho[S], ke[S];
+  const ff gm1 = ff_from_double(gamma - 1.0), half = {0.5f, 0.f}, zero = {0.f, 0.f};
+  ff rho[S], ke[S];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     // b[i2][s1][s0] = sum_i1 I[s1][i1] sum_i0 I[s0][i0] q[i2][i1][i0]
-    double b[NZ][3][3];
+    ff b[NZ][3][3];
 #pragma unroll
     for (int i2 = 0; i2 < NZ; ++i2) {
-      double a[NP][3];
+      ff a[NP][3];
 #pragma unroll
       for (int i1 = 0; i1 < NP; ++i1) {
-        double x[NP];
+        ff x[NP];
 #pragma unroll
-        for (int i0 = 0; i0 < NP; ++i0) x[i0] = q[v * N + (i2 * NP + i1) * NP + i0];
+        for (int i0 = 0; i0 < NP; ++i0) x[i0] = ff_from_double(q[v * N + (i2 * NP + i1) * NP + i0]);
 #pragma unroll
         for (int s0 = 0; s0 < 3; ++s0) {
-          double acc = 0.0;
+          ff acc = zero;
 #pragma unroll
-          for (int i0 = 0; i0 < NP; ++i0) acc = fma(I3.m[s0][i0], x[i0], acc);
+          for (int i0 = 0; i0 < NP; ++i0) acc = fma_t(I3.m[s0][i0], x[i0], acc);
           a[i1][s0] = acc;
         }
       }
@@ -104,46 +110,51 @@ __global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, 
       for (int s1 = 0; s1 < 3; ++s1)
 #pragma unroll
         for (int s0 = 0; s0 < 3; ++s0) {
-          double acc = 0.0;
+          ff acc = zero;
 #pragma unroll
-          for (int i1 = 0; i1 < NP; ++i1) acc = fma(I3.m[s1][i1], a[i1][s0], acc);
+          for (int i1 = 0; i1 < NP; ++i1) acc = fma_t(I3.m[s1][i1], a[i1][s0], acc);
           b[i2][s1][s0] = acc;
         }
     }
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       const int s0 = t % 3, s1 = (t / 3) % 3, s2 = t / 9;
-      double c;
+      ff c;
       if (DIM == 2) {
         c = b[0][s1][s0];
       } else {
-        c = 0.0;
+        c = zero;
 #pragma unroll
-        for (int i2 = 0; i2 < NZ; ++i2) c = fma(I3.m[s2][i2], b[i2][s1][s0], c);
+        for (int i2 = 0; i2 < NZ; ++i2) c = fma_t(I3.m[s2][i2], b[i2][s1][s0], c);
       }
       if (v == 0) {
         rho[t] = c;
-        ke[t] = 0.0;
+        ke[t] = zero;
       } else if (v < NV - 1) {
-        ke[t] = fma(c, c, ke[t]);
+        ke[t] = fma_t(c, c, ke[t]);
       } else {
-        ke[t] = (gamma - 1.0) * (c - 0.5 * ke[t] / rho[t]);  // pressure
+        ke[t] = gm1 * (c - half * ke[t] / rho[t]);  // pressure
       }
     }
   }
-  double rm = 0.0, pm = 0.0;
+  ff rm = zero, pm = zero;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    rm += rho[t];
-    pm += ke[t];
+    rm = rm + rho[t];
+    pm = pm + ke[t];
   }
-  rm /= S;
-  pm /= S;
+  // 100 (q_t - mean) / mean = (q_t - mean) * (100 S / sum)
+  const ff hs = ff_from_double(100.0 * S);
+  const ff fr_ = hs / rm, fp_ = hs / pm;
+  const ff inv_s = ff_from_double(1.0 / S);
+  rm = rm * inv_s;
+  pm = pm * inv_s;
   __nv_bfloat16* x = X + e * IN;
 #pragma unroll
   for (int t = 0; t < S; ++t) {
-    x[t] = __float2bfloat16_rn(float(100.0 * (rho[t] - rm) / rm));
-    x[S + t] = __float2bfloat16_rn(float(100.0 * (ke[t] - pm) / pm));
+    const ff dr = (rho[t] - rm) * fr_, dp = (ke[t] - pm) * fp_;
+    x[t] = __float2bfloat16_rn(dr.h + dr.l);
+    x[S + t] = __float2bfloat16_rn(dp.h + dp.l);
   }
   int span = g.Dmax - Dbase > 0 ? g.Dmax - Dbase : 1;
   x[2 * S] = __float2bfloat16_rn(float(g.depth(keys[e]) - Dbase) / float(span));
@@ -608,7 +619,8 @@ int mlp_features(int dim, int p, const double* u, const uint64_t* keys, int64_t 
       double pr = 1.0;
       for (int k = 0; k < np; ++k)
         if (k != j) pr *= (g3[t] - ops.x[k]) / (ops.x[j] - ops.x[k]);
-      I3.m[t][j] = pr;
+      const float h = float(pr);  // double-word constant: hi + lo
+      I3.m[t][j] = ff{h, float(pr - double(h))};
     }
   unsigned nb = unsigned((M + 127) / 128);
   __nv_bfloat16* X = static_cast<__nv_bfloat16*>(d_X);
