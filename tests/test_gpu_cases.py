@@ -136,3 +136,41 @@ def test_balance_pass_beyond_octant_capacity():
     assert rel_l2(g.state(), o.state()) < 1e-13
     for a, b in zip(g.conn(), O.conn(2, 9, o.leaves())):
         assert np.array_equal(a, b)
+
+
+def test_full_size_2d_p3_workload():
+    # the benchmark's configuration at full size (11k-20k leaves), through the same calls it times:
+    # three cycles of 10 SSP-RK3 steps and an adaptation, compared whole against the oracle
+    cfg = _cfg("vortex2d_p3")
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves()) and g.M > 10000
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    for _ in range(3):
+        g.step(10)
+        o.step(10)
+        assert rel_l2(g.state(), o.state()) < 1e-10
+        fo, _ = o.flags()
+        g.adapt(fo)
+        o.adapt(fo)
+        assert np.array_equal(g.leaves(), o.leaves())
+        assert rel_l2(g.state(), o.state()) < 1e-10
+    ng, no = g.norms(), o.norms()
+    assert abs(ng["l2_rho"] - no["l2_rho"]) < 1e-8 * no["l2_rho"]
+
+
+def test_full_size_3d_tube_workload():
+    # the 3D p=2 tube at full size (177k leaves): initial mesh, one step and one adaptation
+    cfg = _cfg("vortex3d_p2_tube")
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves()) and g.M > 150000
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    g.step(1)
+    o.step(1)
+    assert rel_l2(g.state(), o.state()) < 1e-12
+    fo, _ = o.flags()
+    g.adapt(fo)
+    o.adapt(fo)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-12
