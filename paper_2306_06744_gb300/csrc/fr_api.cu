@@ -142,7 +142,6 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   int64_t* cnt = Sc.get<int64_t>(n_ub);
   int64_t* off = Sc.get<int64_t>(n_ub);
   if (!cnt || !off) return set_error(err, FR_ENOMEM, "conn scratch");
-  FR_CUDA(err, cudaMemsetAsync(m->contrib.p, 0xff, size_t(S) * 16, s));
   FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
   if (m->dim == 2)
     launch_dependent(k_face_count<2>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
@@ -355,8 +354,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<double> nu;
   Buf<int32_t> src, hcon;
   Buf<int8_t> tag;
-  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, m->A, s, err);
-  if (!rc) rc = cudaMemsetAsync(bad, 0, 8, s) == cudaSuccess ? 0 : set_error(err, FR_ECUDA, "memset");
+  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
     int r = 0;
@@ -964,7 +962,7 @@ static int balance_or_adapt(int dim, int Dbase, int Dmax, const uint64_t* d_keys
   int64_t h_ctl[CTL_SLOTS] = {n};
   int64_t n_ub = n;
   if (d_flags) {
-    rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, ctl, A, s, err);
+    rc = tree_edit(dim, g, Dbase, d_keys, d_flags, n, k, ctl, nullptr, A, s, err);
     n_ub = n << dim;
   } else {
     rc = k.ensure(A, n);

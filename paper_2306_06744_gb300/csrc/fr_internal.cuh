@@ -296,10 +296,12 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf
 // [2] refined leaves, [3] coarsened groups, [4] overflowed pass depth (0: none), [5] passes that
 // changed the tree, [6] face-list counts (conforming | hanging << 32).
 enum { CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6, CTL_SLOTS = 8 };
-// The edit zeroes the control block and leaves its leaf count and statistics there without a
-// host synchronisation; its output holds at most n << dim leaves.
+// The edit zeroes the control block (and the two error flags d_bad, if given) and leaves its
+// leaf count and statistics there without a host synchronisation; its output holds at most
+// n << dim leaves.
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
-              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, Alloc& A, cudaStream_t s, Err* err);
+              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
+              Err* err);
 // balances `keys` in place for depth passes D = Dhigh .. Dlow with exact sizes (one host
 // synchronisation per pass); the leaf count is d_ctl[0] on entry (at most n_ub) and h_ctl
 // (CTL_SLOTS values) holds the final control block on return

@@ -66,9 +66,14 @@ __global__ void k_compact(const uint64_t* __restrict__ k, const int32_t* __restr
 template <int DIM>
 __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __restrict__ flags,
                              int64_t n, KG g, int Dbase, int8_t* __restrict__ act,
-                             int32_t* __restrict__ cnt) {
+                             int32_t* __restrict__ cnt, int64_t* __restrict__ ctl,
+                             int32_t* __restrict__ flags_out) {
   pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i == 0) {  // the adaptation's control block and error flags start at zero
+    for (int c = 0; c < CTL_SLOTS; ++c) ctl[c] = 0;
+    if (flags_out) flags_out[0] = flags_out[1] = 0;
+  }
   if (i >= n) return;
   constexpr int NC = 1 << DIM;
   uint64_t key = k[i];
@@ -424,6 +429,7 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
       if (s == 0) first = int(m);
       if (contrib) contrib[t * 4 + s] = int32_t(m);
     }
+    if (contrib && DIM == 2) contrib[t * 4 + 2] = contrib[t * 4 + 3] = -1;  // 2 contributors in 2D
     nbr[t] = first;
   }
 }
@@ -625,7 +631,8 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys, int64_t n, Buf<uint64
 }
 
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
-              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, Alloc& A, cudaStream_t s, Err* err) {
+              int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
+              Err* err) {
   Scratch S(&A);
   int8_t* act = S.get<int8_t>(n);
   int32_t* cnt = S.get<int32_t>(n);
@@ -634,8 +641,8 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   // the edited tree has at most 2^dim leaves per old leaf: the output is sized for that bound and
   // the leaf count stays on the device for the balance passes
   FR_TRY(out.ensure(A, size_t(n) << dim));
-  FR_CUDA(err, cudaMemsetAsync(d_ctl, 0, CTL_SLOTS * sizeof(int64_t), s));
-  DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt)));
+  DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt,
+                                      d_ctl, d_bad)));
   FR_LAUNCH_CHECK(err);
   FR_TRY(scan_counts(cnt, offs, n, d_ctl + CTL_N, S, s, err));
   DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, offs, n, g, out.p,

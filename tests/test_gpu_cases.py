@@ -174,3 +174,21 @@ def test_full_size_3d_tube_workload():
     o.adapt(fo)
     assert np.array_equal(g.leaves(), o.leaves())
     assert rel_l2(g.state(), o.state()) < 1e-12
+
+
+def test_four_tube_3d_p3_reduced_levels():
+    # the four-tube 3D p=3 configuration (four seeded vortices, periodic [0,80]^3) on levels 3-5:
+    # initial mesh, two steps and an adaptation against the oracle
+    cfg = _cfg("vortex3d_p3_multi", Dbase=3, Dmax=5)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves()) and g.M > 1000
+    assert rel_l2(g.state(), o.state()) < 1e-13
+    g.step(2)
+    o.step(2)
+    assert rel_l2(g.state(), o.state()) < 1e-12
+    fo, _ = o.flags()
+    g.adapt(fo)
+    o.adapt(fo)
+    assert np.array_equal(g.leaves(), o.leaves())
+    assert rel_l2(g.state(), o.state()) < 1e-12
