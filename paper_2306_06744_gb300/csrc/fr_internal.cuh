@@ -55,6 +55,10 @@ __device__ __forceinline__ void pdl_wait_then_release() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// Reads issued before pdl_wait_then_release may only touch data final before the predecessor
+// started (its own predecessor's outputs, or static tables): a kernel releases its dependents only
+// after its own wait, so when a kernel starts early, everything but its immediate predecessor has
+// completed.  Writes always come after the wait.
 
 template <class Kern, class... Args>
 cudaError_t launch_dependent(Kern kernel, unsigned grid, unsigned block, cudaStream_t s, Args... args) {

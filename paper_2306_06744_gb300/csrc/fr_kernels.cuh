@@ -337,10 +337,12 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   const int tid = threadIdx.x;
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
   const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
-  pdl_wait_then_release();
+  // the stage's input state and the keys come from earlier launches than the interface kernel
+  // this one depends on: they are read while that kernel drains; the common fluxes after it
   for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
-  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
+  pdl_wait_then_release();
+  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   __syncthreads();
   const int le = tid / N, i = tid % N;
   const bool act = le < ne;
