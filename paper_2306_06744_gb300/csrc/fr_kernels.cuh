@@ -207,7 +207,8 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   T* fcomm = static_cast<T*>(A.fcomm);
   const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
   const int tid = threadIdx.x;
-  pdl_wait_then_release();
+  // the face lists and neighbour tables are fixed during a time step: they are read while the
+  // element kernel this one depends on drains; the traces it wrote are read after the wait
   if (int64_t(blockIdx.x) >= A.nb_hang) {
     int64_t idx = (int64_t(blockIdx.x) - A.nb_hang) * BT + tid;
     int64_t face = idx / NF;
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
     int64_t e = code >> 2;
     int axis = code & 3;
     int64_t nb = A.nbr[e * NFC + 2 * axis + 1];
+    pdl_wait_then_release();
     T qL[NV], qR[NV], F[NV];
     const T* tL = trace + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
     const T* tR = trace + ((nb * NFC + 2 * axis) * NV) * NF + q;
@@ -239,14 +241,17 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   const int lf = tid / PER, r = tid % PER, s = r / NF, q = r % NF;
   const int64_t hf = hb * FPB + lf;
   const bool act = lf < FPB && hf < A.n_hang;
-  int64_t ec = 0;
+  int64_t ec = 0, ek = 0;
   int fc = 0;
   if (act) {
-    int32_t code = A.hang[hf];
+    const int32_t code = A.hang[hf];
     ec = code >> 3;
     fc = code & 7;
+    ek = A.contrib[hf * 4 + s];
+  }
+  pdl_wait_then_release();
+  if (act) {
     int axis = fc >> 1, sidec = fc & 1;
-    int64_t ek = A.contrib[hf * 4 + s];
     int fk = fc ^ 1;
     const T* tc = trace + ((ec * NFC + fc) * NV) * NF;
     T uc[NV], uf[NV], F[NV];
