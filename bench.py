@@ -177,6 +177,53 @@ def run_reference(args):
     return 0
 
 
+def run_tree(args):
+    """Tree completion from a point cloud and 2:1 balance (the paper's meshing benchmark, Sec. 5.1;
+    a seeded torus surface stands in for its scanned model): wall time of each library call,
+    including the host copies of its input and result, best of 3 after a warm-up; the oracle's
+    times on the same points are the CPU baseline, and the outputs are compared bit for bit."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_2306_06744_gb300 import fr
+    from paper_2306_06744_gb300 import workloads as W
+
+    def best(f, reps=3):
+        r = f()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r = f()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - a)
+        return r, min(ts)
+
+    for Dmin, Dmax, n in ((4, 9, 600_000), (4, 10, 2_000_000)):
+        pts = W.torus_points(n, 11)
+        keys, t_c = best(lambda: fr.tree_complete(3, Dmin, Dmax, 1.0, pts))
+        bal, t_b = best(lambda: fr.tree_balance(3, Dmax, keys))
+        line = {"metric": "tree completion + 2:1 balance wall time", "mode": "tree",
+                "value": 1e3 * (t_c + t_b), "unit": "ms", "higher_is_better": False,
+                "complete_ms": 1e3 * t_c, "balance_ms": 1e3 * t_b,
+                "ns_per_balanced_leaf": 1e9 * t_b / len(bal),
+                "config": {"workload": "torus surface points, seed 11", "dim": 3, "points": n,
+                           "Dmin": Dmin, "Dmax": Dmax, "completed_leaves": int(len(keys)),
+                           "balanced_leaves": int(len(bal))}}
+        if not args.no_cpu_baseline:
+            a = time.perf_counter()
+            okeys = O.tree_complete(3, Dmin, Dmax, 1.0, pts)
+            b = time.perf_counter()
+            obal = O.balance(3, Dmax, okeys)
+            c = time.perf_counter()
+            line["cpu_baseline"] = {"value": 1e3 * (c - a), "unit": "ms", "cores": 1, "kind": "oracle",
+                                    "complete_ms": 1e3 * (b - a), "balance_ms": 1e3 * (c - b),
+                                    "sample": "the same points, once"}
+            line["bit_exact"] = bool(np.array_equal(keys, okeys) and np.array_equal(bal, obal))
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def aggregate_ranks(units, seconds, device="cuda"):
     """Whole-job throughput inputs over the ranks of a replica run: the units every rank
     processed, summed, and the slowest rank's time (one rank: unchanged)."""
@@ -230,6 +277,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-forms", action="store_true")
     from paper_2306_06744_gb300 import workloads as W
+    ap.add_argument("--tree", action="store_true",
+                    help="instead: tree completion + 2:1 balance of a 3D point cloud, with the oracle beside it")
     ap.add_argument("--workload", default=WORKLOAD, choices=list(W.CONFIG_NAMES),
                     help="configuration to measure (default: the 2D p=3 vortex the metric is quoted on)")
     args = ap.parse_args()
@@ -238,6 +287,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.tree:
+        return run_tree(args)
 
     import numpy as np
     import torch

@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(1024) k_sort_small(uint64_t* __restrict__ keys
 // Every generated octant lies strictly inside one current leaf, and the octants inside a leaf
 // cover it once linearised (path splitting emits all 2^dim children at each level), so a leaf
 // with a non-empty range [lo, hi) is replaced by the linearised octants of that range and any
-// other leaf is kept.  Linearisation keeps S[r] unless S[r+1] equals it or lies inside it.
+// other leaf is kept.  Linearisation keeps S[r] unless S[r+1] equals it or lies inside it; a set
+// already linearised (`linearised`) is copied range by range.
 template <int DIM>
 __device__ __forceinline__ bool lin_keep(const uint64_t* __restrict__ S, int64_t nS, const KG& g, int64_t r) {
   if (r + 1 >= nS) return true;
@@ -299,7 +300,7 @@ __device__ __forceinline__ bool lin_keep(const uint64_t* __restrict__ S, int64_t
 template <int DIM>
 __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl,
                               int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
-                              int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
+                              bool linearised, int32_t* __restrict__ cnt, int64_t* __restrict__ lo_out) {
   pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
@@ -315,8 +316,12 @@ __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t* __restric
   int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
   int32_t c = 1;
   if (hi > lo) {
-    c = 0;
-    for (int64_t r = lo; r < hi; ++r) c += lin_keep<DIM>(S, nS, g, r);
+    if (linearised) {
+      c = int32_t(hi - lo);
+    } else {
+      c = 0;
+      for (int64_t r = lo; r < hi; ++r) c += lin_keep<DIM>(S, nS, g, r);
+    }
   }
   cnt[i] = c;
   lo_out[i] = hi > lo ? lo : -1;  // -1: the leaf is kept as it is
@@ -325,8 +330,9 @@ __global__ void k_merge_count(const uint64_t* __restrict__ k, int64_t* __restric
 template <int DIM>
 __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                               int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
-                              const int32_t* __restrict__ cnt, const int64_t* __restrict__ lo,
-                              const int64_t* __restrict__ offs, uint64_t* __restrict__ out) {
+                              bool linearised, const int32_t* __restrict__ cnt,
+                              const int64_t* __restrict__ lo, const int64_t* __restrict__ offs,
+                              uint64_t* __restrict__ out) {
   pdl_wait_then_release();
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
@@ -338,8 +344,12 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
     return;
   }
   const int64_t nS = bal_nS(ctl, cap), end = o + c;
-  for (int64_t r = l; o < end; ++r)
-    if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
+  if (linearised) {
+    for (int64_t r = l; o < end; ++r) out[o++] = S[r];
+  } else {
+    for (int64_t r = l; o < end; ++r)
+      if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
+  }
 }
 
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
@@ -680,15 +690,34 @@ static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<ui
     FR_TRY(tmp.ensure(A, size_t(exact_G)));
     FR_TRY(radix_sort_keys(gen.p, tmp.p, exact_G, dim * g.Dmax + g.mb, S, s, err));
   }
+  // with exact sizes (large sets, which carry many duplicate requests) the generated octants are
+  // linearised in parallel first, their count replacing ctl[CTL_G]; small sets are linearised
+  // inside the merge, range by range
+  const bool lin_first = exact_G >= 0;
+  const uint64_t* src = gen.p;
+  if (lin_first) {
+    int32_t* cl = S.get<int32_t>(exact_G);
+    int64_t* ol = S.get<int64_t>(exact_G);
+    if (!cl || !ol) return set_error(err, FR_ENOMEM, "balance linearise scratch");
+    FR_TRY(tmp.ensure(A, size_t(exact_G)));
+    DIM_DISPATCH(dim, (k_lin_count<D_><<<nblk(exact_G), TB, 0, s>>>(gen.p, exact_G, g, cl)));
+    FR_LAUNCH_CHECK(err);
+    FR_TRY(scan_counts(cl, ol, exact_G, d_ctl + CTL_G, S, s, err));
+    k_compact<<<nblk(exact_G), TB, 0, s>>>(gen.p, cl, ol, exact_G, tmp.p);
+    FR_LAUNCH_CHECK(err);
+    src = tmp.p;
+  }
   int32_t* cnt2 = S.get<int32_t>(n_ub);
   int64_t* lo = S.get<int64_t>(n_ub);
   int64_t* offs2 = S.get<int64_t>(n_ub);
   if (!cnt2 || !lo || !offs2) return set_error(err, FR_ENOMEM, "balance merge scratch");
-  DIM_DISPATCH(dim, (launch_dependent(k_merge_count<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo)));
+  DIM_DISPATCH(dim, (launch_dependent(k_merge_count<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, src, cap, g,
+                                      lin_first, cnt2, lo)));
   FR_LAUNCH_CHECK(err);
   // the merged tree has at most n + G leaves; its count replaces ctl[CTL_N] on the device
   FR_TRY(scan_counts(cnt2, offs2, n_ub, d_ctl + CTL_N, S, s, err));
-  DIM_DISPATCH(dim, (launch_dependent(k_merge_write<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, gen.p, cap, g, cnt2, lo, offs2, out.p)));
+  DIM_DISPATCH(dim, (launch_dependent(k_merge_write<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, src, cap, g,
+                                      lin_first, cnt2, lo, offs2, out.p)));
   FR_LAUNCH_CHECK(err);
   Buf<uint64_t> t = keys;  // the merged tree becomes the tree
   keys = out;

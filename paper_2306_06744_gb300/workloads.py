@@ -152,6 +152,25 @@ def random_flags(n: int, seed: int, p_refine: float = 0.2, p_coarsen: float = 0.
 
 
 def random_uniform(n: int, seed: int) -> np.ndarray:
-    """n seeded uniforms in [0,1) (used for smooth state perturbations in tests)."""
-    rng = SplitMix64(seed)
-    return np.array([rng.uniform() for _ in range(n)], dtype=np.float64)
+    """n seeded uniforms in [0,1): the first n draws of SplitMix64(seed), vectorised (the k-th
+    state is seed + k * gamma modulo 2^64)."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = np.uint64(seed & _MASK) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def torus_points(n: int, seed: int, dim: int = 3, L: float = 1.0) -> np.ndarray:
+    """n seeded points on a torus surface (3D: radii 0.28 and 0.1 about the centre of the box) or a
+    circle (2D: radius 0.3), inside [0, L)^dim: a synthetic stand-in for a scanned surface."""
+    u = random_uniform(2 * n, seed).reshape(n, 2) * 2 * np.pi
+    if dim == 2:
+        return np.stack([0.5 + 0.3 * np.cos(u[:, 0]), 0.5 + 0.3 * np.sin(u[:, 0])], 1) * L
+    R, r = 0.28, 0.1
+    x = (R + r * np.cos(u[:, 1])) * np.cos(u[:, 0])
+    y = (R + r * np.cos(u[:, 1])) * np.sin(u[:, 0])
+    z = r * np.sin(u[:, 1])
+    return (np.stack([x, y, z], 1) + 0.5) * L

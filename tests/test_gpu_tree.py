@@ -106,18 +106,6 @@ def test_large_balance_sampled():
     assert np.array_equal(got, want)
 
 
-def _surface_points(n, seed, dim=3, L=1.0):
-    """Seeded points on a torus (3D) or circle (2D) surface inside [0,L)^dim."""
-    u = W.random_uniform(2 * n, seed).reshape(n, 2) * 2 * np.pi
-    if dim == 2:
-        return np.stack([0.5 + 0.3 * np.cos(u[:, 0]), 0.5 + 0.3 * np.sin(u[:, 0])], 1) * L
-    R, r = 0.28, 0.1
-    x = (R + r * np.cos(u[:, 1])) * np.cos(u[:, 0])
-    y = (R + r * np.cos(u[:, 1])) * np.sin(u[:, 0])
-    z = r * np.sin(u[:, 1])
-    return (np.stack([x, y, z], 1) + 0.5) * L
-
-
 @pytest.mark.parametrize("dim,Dmin,Dmax,n,kind", [(2, 2, 8, 500, "uniform"), (2, 3, 12, 3000, "surface"),
                                                   (3, 1, 6, 800, "uniform"), (3, 4, 9, 20000, "surface"),
                                                   (3, 2, 5, 0, "uniform"), (2, 0, 10, 1, "uniform")])
@@ -126,7 +114,7 @@ def test_tree_complete(dim, Dmin, Dmax, n, kind):
     if kind == "uniform":
         pts = W.random_uniform(n * dim, 5 + n).reshape(n, dim) * L
     else:
-        pts = _surface_points(n, 9, dim, L)
+        pts = W.torus_points(n, 9, dim, L)
     got = fr.tree_complete(dim, Dmin, Dmax, L, pts)
     want = O.tree_complete(dim, Dmin, Dmax, L, pts)
     assert np.array_equal(got, want)

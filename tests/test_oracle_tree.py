@@ -258,3 +258,14 @@ def test_tree_complete_closed_forms():
         assert len(O.tree_complete(dim, 2, 5, 1.0, np.zeros((0, dim)))) == (1 << (dim * 2))
         one = O.tree_complete(dim, 2, 5, 1.0, np.full((1, dim), 0.3))
         assert len(one) == (1 << (dim * 2)) + ((1 << dim) - 1) * (5 - 2)
+
+
+def test_vectorised_draws_match_splitmix64():
+    # the seeded input generator shared by tests and benchmark: vectorised draws = the scalar
+    # SplitMix64 sequence, including a seed near 2^64 (wrap-around)
+    for seed in (0, 7, 2 ** 64 - 3):
+        r = W.SplitMix64(seed)
+        want = np.array([r.uniform() for _ in range(257)])
+        assert np.array_equal(W.random_uniform(257, seed), want)
+    p = W.torus_points(1000, 3)
+    assert p.shape == (1000, 3) and p.min() > 0.0 and p.max() < 1.0
