@@ -179,7 +179,9 @@ const char* fr_last_error(const fr_mesh* m);
    fr_mlp_forward (and the mesh's learned indicator) runs on the tensor cores: BF16 MMAs with FP32
    accumulators in tensor memory, over tiles of 128 feature rows; a completion wait that gives up
    after about a second returns FR_ETIMEOUT (from fr_adapt/fr_run when it happens inside the
-   indicator).  Training runs on the CUDA cores. */
+   indicator).  fr_mlp_grad and fr_mlp_train_step run on the tensor cores too (batch tiles of 128
+   samples, weight gradients accumulated in tensor memory, block partials summed in a fixed order:
+   deterministic), with the same FR_ETIMEOUT behaviour. */
 int fr_mlp_param_count(int in_dim);
 int fr_features(fr_mesh* m, void* d_X_bf16, int64_t cap, int32_t* in_dim);
 int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n);

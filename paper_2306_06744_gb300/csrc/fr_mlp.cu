@@ -10,10 +10,9 @@
 // relative deviations from their means scaled by 100 (a 1% variation is 1.0), then the depth as
 // (D - Dbase) / max(1, Dmax - Dbase): IN = 2*3^dim + 1 inputs (19 in 2D, 55 in 3D).
 //
-// Inference runs on the tensor cores (tcgen05, BF16 operands in shared memory, FP32 accumulators
-// in tensor memory): batched over elements the layers are dense [128 x 64] x [64 x 64]
-// contractions.  Training (per-sample forward/backward and the weight-gradient reduction) runs on
-// the CUDA cores with FP32 FMA on BF16-rounded operands.
+// Inference and training run on the tensor cores (tcgen05, BF16 operands in shared memory, FP32
+// accumulators in tensor memory): batched over elements the layers are dense [128 x 64] x [64 x 64]
+// contractions, and the weight gradients [64 x 128] x [128 x 64] contractions over the samples.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -29,7 +28,6 @@ namespace {
 
 constexpr int H = MLP_HIDDEN;
 constexpr int NOUT = 3;
-constexpr int MLP_T = 128;  // threads (samples) per block
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
@@ -158,48 +156,6 @@ __global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, 
   }
   int span = g.Dmax - Dbase > 0 ? g.Dmax - Dbase : 1;
   x[2 * S] = __float2bfloat16_rn(float(g.depth(keys[e]) - Dbase) / float(span));
-}
-
-// shared-memory copy of the BF16-rounded weights as floats
-__device__ void load_weights(const float* __restrict__ P, int total, float* sw) {
-  for (int k = threadIdx.x; k < total; k += blockDim.x) sw[k] = bf16r(P[k]);
-}
-
-// first layer: z[i] = b[i] + sum_k W[i][k] x_k, x read from the BF16 input row
-__device__ __forceinline__ void layer_in(const float* W, const float* b, const __nv_bfloat16* x,
-                                         int in, float (&z)[H]) {
-#pragma unroll
-  for (int i = 0; i < H; ++i) z[i] = b[i];
-  for (int k = 0; k < in; ++k) {
-    float xk = __bfloat162float(x[k]);
-#pragma unroll
-    for (int i = 0; i < H; ++i) z[i] = fmaf(W[i * in + k], xk, z[i]);
-  }
-}
-// hidden layer: z[i] = b[i] + sum_k W[i][k] a_k
-__device__ __forceinline__ void layer_h(const float* W, const float* b, const float (&a)[H],
-                                        float (&z)[H]) {
-#pragma unroll
-  for (int i = 0; i < H; ++i) z[i] = b[i];
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-#pragma unroll
-    for (int i = 0; i < H; ++i) z[i] = fmaf(W[i * H + k], a[k], z[i]);
-  }
-}
-__device__ __forceinline__ void act(const float (&z)[H], float (&a)[H]) {
-#pragma unroll
-  for (int i = 0; i < H; ++i) a[i] = bf16r(gelu(z[i]));
-}
-__device__ __forceinline__ void layer_out(const float* W, const float* b, const float (&a)[H],
-                                          float (&z)[NOUT]) {
-#pragma unroll
-  for (int c = 0; c < NOUT; ++c) {
-    float t = b[c];
-#pragma unroll
-    for (int k = 0; k < H; ++k) t = fmaf(W[c * H + k], a[k], t);
-    z[c] = t;
-  }
 }
 
 // Tensor-core forward.  Each block keeps the four weight matrices in shared memory as BF16 in the
@@ -406,136 +362,292 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
   }
 }
 
-// training, per sample: forward, weighted softmax cross-entropy, backward to every layer's
-// pre-activation gradient.  Stores the inputs of every layer (A0..A3), the pre-activations
-// (Z1..Z3) and the gradients (D1..D4) for the weight-gradient reduction, and the sample's loss.
-__global__ void __launch_bounds__(MLP_T) k_mlp_fwd_bwd(const float* __restrict__ P, int in,
-                                                       const __nv_bfloat16* __restrict__ X,
-                                                       const int8_t* __restrict__ y, int64_t B,
-                                                       float cw0, float cw1, float cw2, float inv_wsum,
-                                                       float* __restrict__ A, float* __restrict__ Z,
-                                                       float* __restrict__ D, float* __restrict__ loss) {
-  extern __shared__ float sw[];
+// Tensor-core training: gradient of the weighted mean softmax cross-entropy over a batch.  Each
+// block (one per SM: 206 KB of shared memory, all 512 tensor-memory columns) loops over tiles of
+// 128 samples.  Forward as in inference, keeping every layer's input A_l in shared memory both row
+// by row (the A operand of the next layer) and transposed (AT_l, the B operand of the weight
+// gradient).  Backward, layer by layer from the output: the error signal dZ (BF16) is written both
+// row by row (DZ, the A operand of dA = dZ W) and transposed (DZT), and one thread issues
+//   dW_l += DZT * AT_{l-1}^T   (M = 128 with rows 0..63 used, K = 128 samples; accumulated in
+//                               tensor memory over all the block's tiles),
+//   dA_{l-1} = DZ * W_l        (B operand W_l^T, a transposed copy),
+//   Z_{l-1} = A_{l-2} W_{l-1}^T  (the pre-activation recomputed instead of stored),
+// after which each thread forms its row of dZ_{l-1} = dA_{l-1} * GELU'(Z_{l-1} + b).  Bias
+// gradients are the row sums of DZT (thread o sums row o, in a fixed order).  Samples past the
+// end of the batch get dZ = 0.  At the end the block writes its partial gradient and loss; a
+// second kernel sums the blocks' partials in block order (deterministic).  Waits are bounded as
+// in inference (status word, drain, free).
+constexpr int TG_ROWS = 128, TG_TMEM_COLS = 512;
+constexpr int TG_W1 = 0, TG_W2 = 8192, TG_W3 = 16384, TG_W4 = 24576, TG_W2T = 26624, TG_W3T = 34816,
+              TG_W4T = 43008, TG_DZT = 45056, TG_A0 = 61440, TG_AT0 = 126976, TG_DZ = 192512,
+              TG_BIAS = 208896, TG_MBAR = TG_BIAS + 208 * 4, TG_SMEM = TG_MBAR + 16 + 1024;
+// DZT is followed by A0, which the M = 128 weight-gradient products read as rows 64..127 of their
+// A operand: those rows only reach rows 64..127 of the accumulators, which are never read
+
+__global__ void __launch_bounds__(TG_ROWS) k_mlp_grad_tc(const float* __restrict__ P, int in,
+                                                         const __nv_bfloat16* __restrict__ X,
+                                                         const int8_t* __restrict__ y, int64_t B, float cw0,
+                                                         float cw1, float cw2, float inv_wsum,
+                                                         float* __restrict__ Gp, float* __restrict__ Lp,
+                                                         int* __restrict__ status) {
+  extern __shared__ unsigned char sm_raw[];
+  unsigned char* sm = sm_raw + ((1024 - (tc::smem_addr(sm_raw) & 1023)) & 1023);
+  const int t = threadIdx.x, warp = t >> 5;
   const Lay L = lay(in);
-  load_weights(P, L.total, sw);
+  const int K1 = in <= 32 ? 32 : 64;
+  auto put = [&](int off, uint32_t o, float v) {
+    *reinterpret_cast<__nv_bfloat16*>(sm + off + o) = __float2bfloat16_rn(v);
+  };
+  // weights (BF16, zero padding) and their transposes for the backward products
+  for (int idx = t; idx < H * 64; idx += TG_ROWS) {
+    const int o = idx >> 6, k = idx & 63;
+    put(TG_W1, tc::canon_off(o, k), k < in ? P[L.oW1 + o * in + k] : 0.f);
+    const float w2 = P[L.oW2 + o * H + k], w3 = P[L.oW3 + o * H + k];
+    put(TG_W2, tc::canon_off(o, k), w2);
+    put(TG_W3, tc::canon_off(o, k), w3);
+    put(TG_W2T, tc::canon_off(k, o), w2);  // W2T[i][o] = W2[o][i]
+    put(TG_W3T, tc::canon_off(k, o), w3);
+    if (o < 16) {
+      const float w4 = o < NOUT ? P[L.oW4 + o * H + k] : 0.f;
+      put(TG_W4, tc::canon_off(o, k), w4);
+      put(TG_W4T, tc::canon_off_w(k, o, 16), w4);  // W4T[i][c] (16 columns)
+    }
+  }
+  float* sb = reinterpret_cast<float*>(sm + TG_BIAS);
+  for (int i = t; i < H; i += TG_ROWS) {
+    sb[i] = bf16r(P[L.ob1 + i]);
+    sb[H + i] = bf16r(P[L.ob2 + i]);
+    sb[2 * H + i] = bf16r(P[L.ob3 + i]);
+  }
+  if (t < 16) sb[3 * H + t] = t < NOUT ? bf16r(P[L.ob4 + t]) : 0.f;
+  const uint32_t mb = tc::smem_addr(sm + TG_MBAR);
+  if (t == 0) tc::mbar_init(mb, 1);
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(sm + TG_MBAR + 8), TG_TMEM_COLS);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
   __syncthreads();
-  int64_t b = int64_t(blockIdx.x) * MLP_T + threadIdx.x;
-  if (b >= B) return;
-  const int64_t HA = B * H;
-  float* A0 = A;  // B x in, then A1..A3 (B x 64 each)
-  float* A1 = A + B * in;
-  float* A2 = A1 + HA;
-  float* A3 = A2 + HA;
-  float* Z1 = Z;
-  float* Z2 = Z + HA;
-  float* Z3 = Z2 + HA;
-  float* D1 = D;  // B x 64 each, then D4: B x 3
-  float* D2 = D1 + HA;
-  float* D3 = D2 + HA;
-  float* D4 = D3 + HA;
-  const __nv_bfloat16* x = X + b * in;
-  for (int k = 0; k < in; ++k) A0[b * in + k] = __bfloat162float(x[k]);
-  float z[H], a[H], o[NOUT];
-  layer_in(sw + L.oW1, sw + L.ob1, x, in, z);
-  act(z, a);
+  tc::fence_after_sync();
+  const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(sm + TG_MBAR + 8);
+  const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
+  const uint32_t ACC1 = 0, ACC2 = 64, DW[4] = {128, 192, 256, 320};  // tensor-memory columns
+  const uint32_t sa = tc::smem_addr(sm);
+  auto aof = [](int l) { return TG_A0 + l * 16384; };
+  auto atof = [](int l) { return TG_AT0 + l * 16384; };
+  const int woff[4] = {TG_W1, TG_W2, TG_W3, TG_W4};
+  // one thread: D (+)= A * B^T over nk K-steps of 16, A and B tiles with the given row strides
+  auto mma = [&](uint32_t dcol, int aoff, uint32_t asbo, int boff, uint32_t bsbo, int nk, int N, bool acc) {
+    const uint32_t id = tc::idesc_bf16(TG_ROWS, N);
+    for (int ks = 0; ks < nk; ++ks)
+      tc::mma_bf16(tmem + dcol, tc::sdesc(sa + aoff + ks * 2 * tc::LBO, asbo),
+                   tc::sdesc(sa + boff + ks * 2 * tc::LBO, bsbo), id, acc || ks > 0);
+  };
+  uint32_t phase = 0;
+  bool failed = false, pend = false;
+  // issue (thread 0, after the block's writes are visible to the tensor cores), commit, wait
+  auto sync_issue_wait = [&](auto&& issue) -> bool {
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (t == 0) {
+      tc::fence_after_sync();
+      issue();
+      tc::commit(mb);
+    }
+    pend = true;
+    const bool ok = tc::mbar_wait(mb, phase, TC_WAIT_CYCLES);
+    if (__syncthreads_or(!ok)) return false;
+    phase ^= 1;
+    pend = false;
+    tc::fence_after_sync();
+    return true;
+  };
+  const int64_t ntiles = (B + TG_ROWS - 1) / TG_ROWS;
+  float loss = 0.f, db[4] = {0.f, 0.f, 0.f, 0.f};  // thread o: bias gradient o of each layer
+  bool first = true;
+  // thread t's row of dZ (FP32) -> DZ (row t) and DZT (column t), BF16; ncol columns
+  auto put_dz = [&](int c, float v) {
+    put(TG_DZ, tc::canon_off(t, c), v);
+    put(TG_DZT, tc::canon_off_w(c, t, 128), v);
+  };
+  auto sum_dzt_row = [&](int o) {  // fixed-order sum over the 128 samples of row o of DZT
+    float acc = 0.f;
+    for (int j = 0; j < TG_ROWS; j += 8) {
+      const uint4 v = *reinterpret_cast<const uint4*>(sm + TG_DZT + tc::canon_off_w(o, j, 128));
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
 #pragma unroll
-  for (int i = 0; i < H; ++i) {
-    Z1[b * H + i] = z[i];
-    A1[b * H + i] = a[i];
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        acc += f.x;
+        acc += f.y;
+      }
+    }
+    return acc;
+  };
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t row0 = tile * TG_ROWS;
+    const int nrow = int(B - row0 < TG_ROWS ? B - row0 : TG_ROWS);
+    const bool valid = t < nrow;
+    // features: coalesced reads of the tile's contiguous rows into A0 and AT0, zero padding
+    const __nv_bfloat16* xs = X + row0 * in;
+    for (int idx = t; idx < TG_ROWS * in; idx += TG_ROWS) {
+      const int r = idx / in, k = idx - r * in;
+      const __nv_bfloat16 v = r < nrow ? xs[idx] : __float2bfloat16_rn(0.f);
+      *reinterpret_cast<__nv_bfloat16*>(sm + aof(0) + tc::canon_off(r, k)) = v;
+      *reinterpret_cast<__nv_bfloat16*>(sm + atof(0) + tc::canon_off_w(k, r, 128)) = v;
+    }
+    for (int k = in; k < 64; ++k) {
+      if (k < K1) put(aof(0), tc::canon_off(t, k), 0.f);
+      put(atof(0), tc::canon_off_w(k, t, 128), 0.f);
+    }
+    // forward: layers 1..3 into A_l / AT_l, layer 4 to logits
+    for (int l = 0; l < 3 && !failed; ++l) {
+      const int nk = l == 0 ? K1 / 16 : H / 16;
+      if (!sync_issue_wait([&] { mma(ACC1, aof(l), tc::SBO, woff[l], tc::SBO, nk, H, false); })) {
+        failed = true;
+        break;
+      }
+      const float* bl = sb + H * l;
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        uint32_t r[16];
+        tc::tmem_ld16(tlane + ACC1 + uint32_t(c0), r);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float a = gelu(__uint_as_float(r[j]) + bl[c0 + j]);
+          put(aof(l + 1), tc::canon_off(t, c0 + j), a);
+          put(atof(l + 1), tc::canon_off_w(c0 + j, t, 128), a);
+        }
+      }
+    }
+    if (failed) break;
+    if (!sync_issue_wait([&] { mma(ACC1, aof(3), tc::SBO, TG_W4, tc::SBO, H / 16, 16, false); })) {
+      failed = true;
+      break;
+    }
+    {
+      uint32_t r[16];
+      tc::tmem_ld16(tlane + ACC1, r);
+      tc::tmem_wait_ld();
+      float dz[NOUT] = {0.f, 0.f, 0.f};
+      if (valid) {
+        float o[NOUT];
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) o[c] = __uint_as_float(r[c]) + sb[3 * H + c];
+        const int cls = int(y[row0 + t]) + 1;
+        const float w = cls == 0 ? cw0 : (cls == 1 ? cw1 : cw2);
+        const float mx = fmaxf(o[0], fmaxf(o[1], o[2]));
+        const float e0 = expf(o[0] - mx), e1 = expf(o[1] - mx), e2 = expf(o[2] - mx);
+        const float sum = e0 + e1 + e2;
+        const float pz[NOUT] = {e0 / sum, e1 / sum, e2 / sum};
+        loss += -w * inv_wsum * logf(pz[cls]);
+#pragma unroll
+        for (int c = 0; c < NOUT; ++c) dz[c] = w * inv_wsum * (pz[c] - (c == cls ? 1.f : 0.f));
+      }
+      for (int c = 0; c < 16; ++c) put(TG_DZ, tc::canon_off(t, c), c < NOUT ? dz[c] : 0.f);
+      for (int c = 0; c < NOUT; ++c) put(TG_DZT, tc::canon_off_w(c, t, 128), dz[c]);
+    }
+    // backward: l = 3 (output layer's weights) down to 0
+    for (int l = 3; l >= 0 && !failed; --l) {
+      // dW_l += DZT * AT_{l-1}; for l > 0 also dA = DZ * W_l and the recomputed Z of layer l-1
+      const bool ok = sync_issue_wait([&] {
+        mma(DW[l], TG_DZT, 2048, atof(l), 2048, TG_ROWS / 16, H, !first);
+        if (l > 0) {
+          if (l == 3)
+            mma(ACC1, TG_DZ, tc::SBO, TG_W4T, 256, 1, H, false);
+          else
+            mma(ACC1, TG_DZ, tc::SBO, l == 2 ? TG_W3T : TG_W2T, tc::SBO, H / 16, H, false);
+          mma(ACC2, aof(l - 1), tc::SBO, woff[l - 1], tc::SBO, l - 1 == 0 ? K1 / 16 : H / 16, H, false);
+        }
+      });
+      // bias gradient of layer l from the DZT rows the products above read (no writes yet)
+      if (t < (l == 3 ? NOUT : H)) db[l] += sum_dzt_row(t);
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      if (l == 0) break;
+      __syncthreads();  // every row of DZT summed before it is overwritten
+      // dZ of layer l-1: dA * GELU'(Z + b)
+      const float* bl = sb + H * (l - 1);
+#pragma unroll
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        uint32_t ra[16], rz[16];
+        tc::tmem_ld16(tlane + ACC1 + uint32_t(c0), ra);
+        tc::tmem_ld16(tlane + ACC2 + uint32_t(c0), rz);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float d = valid ? __uint_as_float(ra[j]) * gelu_d(__uint_as_float(rz[j]) + bl[c0 + j]) : 0.f;
+          put_dz(c0 + j, d);
+        }
+      }
+    }
+    first = false;
   }
-  layer_h(sw + L.oW2, sw + L.ob2, a, z);
-  act(z, a);
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-    Z2[b * H + i] = z[i];
-    A2[b * H + i] = a[i];
+  if (failed) {
+    if (t == 0) atomicExch(status, 1);
+    if (pend) tc::mbar_wait(mb, phase, TC_WAIT_CYCLES);
   }
-  layer_h(sw + L.oW3, sw + L.ob3, a, z);
-  act(z, a);
+  __syncthreads();
+  // the block's partial gradient in the parameter layout, and its loss
+  float* g = Gp + int64_t(blockIdx.x) * L.total;
+  if (warp < 2) {  // rows 0..63 of the weight-gradient accumulators (tensor-memory lanes 0..63)
+    tc::fence_after_sync();
+    for (int l = 0; l < 4; ++l) {
+      const int nin = l == 0 ? in : H, ow = l == 0 ? L.oW1 : l == 1 ? L.oW2 : l == 2 ? L.oW3 : L.oW4;
+      const int nout = l == 3 ? NOUT : H;
 #pragma unroll
-  for (int i = 0; i < H; ++i) {
-    Z3[b * H + i] = z[i];
-    A3[b * H + i] = a[i];
+      for (int c0 = 0; c0 < H; c0 += 16) {
+        uint32_t r[16];
+        tc::tmem_ld16(tlane + DW[l] + uint32_t(c0), r);
+        tc::tmem_wait_ld();
+        if (t < nout && !first)
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < nin) g[ow + t * nin + c0 + j] = __uint_as_float(r[j]);
+      }
+    }
   }
-  layer_out(sw + L.oW4, sw + L.ob4, a, o);
-  // softmax cross-entropy with class weights, normalised by the batch's total weight
-  int cls = int(y[b]) + 1;
-  float w = cls == 0 ? cw0 : (cls == 1 ? cw1 : cw2);
-  float mx = fmaxf(o[0], fmaxf(o[1], o[2]));
-  float e0 = expf(o[0] - mx), e1 = expf(o[1] - mx), e2 = expf(o[2] - mx);
-  float sum = e0 + e1 + e2;
-  float pz[NOUT] = {e0 / sum, e1 / sum, e2 / sum};
-  loss[b] = -w * inv_wsum * logf(pz[cls]);
-  float d4[NOUT];
-#pragma unroll
-  for (int c = 0; c < NOUT; ++c) {
-    d4[c] = w * inv_wsum * (pz[c] - (c == cls ? 1.f : 0.f));
-    D4[b * NOUT + c] = d4[c];
+  if (first) {  // a block without tiles contributes zeros
+    for (int k = t; k < L.total; k += TG_ROWS) g[k] = 0.f;
+  } else {
+    if (t < H) {
+      g[L.ob1 + t] = db[0];
+      g[L.ob2 + t] = db[1];
+      g[L.ob3 + t] = db[2];
+    }
+    if (t < NOUT) g[L.ob4 + t] = db[3];
   }
-  // backward: d3 = (W4^T d4) * gelu'(z3), d2 = (W3^T d3) * gelu'(z2), d1 = (W2^T d2) * gelu'(z1)
-  float d[H], g[H];
+  // loss: warp sums, then the four warps in order
+  float* red = reinterpret_cast<float*>(sm + TG_BIAS);
+  __syncthreads();
 #pragma unroll
-  for (int k = 0; k < H; ++k) {
-    float t = 0.f;
-#pragma unroll
-    for (int c = 0; c < NOUT; ++c) t = fmaf(sw[L.oW4 + c * H + k], d4[c], t);
-    d[k] = t * gelu_d(Z3[b * H + k]);
-    D3[b * H + k] = d[k];
+  for (int w = 16; w > 0; w >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, w);
+  if ((t & 31) == 0) red[warp] = loss;
+  __syncthreads();
+  if (t == 0) Lp[blockIdx.x] = red[0] + red[1] + red[2] + red[3];
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, TG_TMEM_COLS);
   }
-#pragma unroll
-  for (int k = 0; k < H; ++k) g[k] = 0.f;
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-#pragma unroll
-    for (int k = 0; k < H; ++k) g[k] = fmaf(sw[L.oW3 + i * H + k], d[i], g[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < H; ++k) {
-    d[k] = g[k] * gelu_d(Z2[b * H + k]);
-    D2[b * H + k] = d[k];
-    g[k] = 0.f;
-  }
-#pragma unroll
-  for (int i = 0; i < H; ++i) {
-#pragma unroll
-    for (int k = 0; k < H; ++k) g[k] = fmaf(sw[L.oW2 + i * H + k], d[i], g[k]);
-  }
-#pragma unroll
-  for (int k = 0; k < H; ++k) D1[b * H + k] = g[k] * gelu_d(Z1[b * H + k]);
 }
 
-// weight gradients, one thread per parameter, summing the batch in index order (deterministic)
-__global__ void k_mlp_wgrad(int in, int64_t B, const float* __restrict__ A, const float* __restrict__ D,
-                            float* __restrict__ G) {
-  const Lay L = lay(in);
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= L.total) return;
-  const int64_t HA = B * H;
-  const float* A0 = A;
-  const float* A1 = A + B * in;
-  const float* A2 = A1 + HA;
-  const float* A3 = A2 + HA;
-  const float* D1 = D;
-  const float* D2 = D1 + HA;
-  const float* D3 = D2 + HA;
-  const float* D4 = D3 + HA;
-  const float *Ad = nullptr, *Dd = nullptr;
-  int nin = 0, nout = H, i = 0, k = -1;
-  if (t < L.ob1) { Ad = A0; Dd = D1; nin = in; i = (t - L.oW1) / in; k = (t - L.oW1) % in; }
-  else if (t < L.oW2) { Dd = D1; i = t - L.ob1; }
-  else if (t < L.ob2) { Ad = A1; Dd = D2; nin = H; i = (t - L.oW2) / H; k = (t - L.oW2) % H; }
-  else if (t < L.oW3) { Dd = D2; i = t - L.ob2; }
-  else if (t < L.ob3) { Ad = A2; Dd = D3; nin = H; i = (t - L.oW3) / H; k = (t - L.oW3) % H; }
-  else if (t < L.oW4) { Dd = D3; i = t - L.ob3; }
-  else if (t < L.ob4) { Ad = A3; Dd = D4; nin = H; nout = NOUT; i = (t - L.oW4) / H; k = (t - L.oW4) % H; }
-  else { Dd = D4; nout = NOUT; i = t - L.ob4; }
-  float s = 0.f;
-  if (k >= 0) {
-    for (int64_t b = 0; b < B; ++b) s = fmaf(Dd[b * nout + i], Ad[b * nin + k], s);
-  } else {
-    for (int64_t b = 0; b < B; ++b) s += Dd[b * nout + i];
+// sums of the blocks' partial gradients and losses, in block order
+__global__ void k_grad_reduce(const float* __restrict__ Gp, const float* __restrict__ Lp, int nblk, int total,
+                              float* __restrict__ G, float* __restrict__ loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < total) {
+    float a = 0.f;
+    for (int c = 0; c < nblk; ++c) a += Gp[int64_t(c) * total + p];
+    G[p] = a;
   }
-  G[t] = s;
+  if (p == 0 && loss) {
+    float a = 0.f;
+    for (int c = 0; c < nblk; ++c) a += Lp[c];
+    *loss = a;
+  }
 }
 
 // Adam (Kingma & Ba): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2, p -= lr mhat / (sqrt(vhat) + eps)
@@ -551,22 +663,6 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __re
   v[t] = vt;
   P[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
 }
-
-// deterministic sum of the per-sample losses (one block, fixed order)
-__global__ void k_sum(const float* __restrict__ x, int64_t n, float* __restrict__ out) {
-  __shared__ float s[256];
-  float a = 0.f;
-  for (int64_t i = threadIdx.x; i < n; i += 256) a += x[i];
-  s[threadIdx.x] = a;
-  __syncthreads();
-  for (int st = 128; st > 0; st >>= 1) {
-    if (int(threadIdx.x) < st) s[threadIdx.x] += s[threadIdx.x + st];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *out = s[0];
-}
-
-size_t fwd_smem(int in) { return sizeof(float) * size_t(lay(in).total); }
 
 }  // namespace
 
@@ -635,61 +731,64 @@ int mlp_features(int dim, int p, const double* u, const uint64_t* keys, int64_t 
   return 0;
 }
 
+// gradient (into G, total floats) and loss of one batch on the tensor cores; *d_st (scratch)
+// becomes nonzero if a completion wait gave up
+static int grad_tc(const float* d_params, int in, const void* d_X, const int8_t* d_y, int64_t B,
+                   const float* cw, float* G, float* d_loss, Scratch& S, int** d_st, cudaStream_t s, Err* err) {
+  if (B <= 0) return set_error(err, FR_EINVAL, "empty batch");
+  if (in < 1 || in > 64) return set_error(err, FR_EINVAL, "the MLP takes 1..64 inputs");
+  const Lay L = lay(in);
+  int dev = 0, sms = 0;
+  FR_CUDA(err, cudaGetDevice(&dev));
+  FR_CUDA(err, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntiles = (B + TG_ROWS - 1) / TG_ROWS;
+  const int grid = int(ntiles < sms ? ntiles : sms);  // one block per SM (shared memory, TMEM)
+  float* Gp = S.get<float>(size_t(grid) * L.total);
+  float* Lp = S.get<float>(size_t(grid));
+  int* st = S.get<int>(1);
+  if (!Gp || !Lp || !st) return set_error(err, FR_ENOMEM, "training scratch");
+  FR_CUDA(err, cudaMemsetAsync(st, 0, 4, s));
+  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM));
+  // class weights normalised by the batch's total weight: cw[0..2], and cw[3] = 1 / sum_b w_{y_b}
+  k_mlp_grad_tc<<<unsigned(grid), TG_ROWS, TG_SMEM, s>>>(d_params, in, static_cast<const __nv_bfloat16*>(d_X),
+                                                         d_y, B, cw[0], cw[1], cw[2], cw[3], Gp, Lp, st);
+  FR_LAUNCH_CHECK(err);
+  k_grad_reduce<<<unsigned((L.total + 255) / 256), 256, 0, s>>>(Gp, Lp, grid, L.total, G, d_loss);
+  FR_LAUNCH_CHECK(err);
+  *d_st = st;
+  return 0;
+}
+
+static int check_status(const int* d_st, cudaStream_t s, Err* err) {
+  int h = 0;
+  FR_CUDA(err, cudaMemcpyAsync(&h, d_st, 4, cudaMemcpyDeviceToHost, s));
+  FR_CUDA(err, cudaStreamSynchronize(s));
+  return h ? set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (training)") : 0;
+}
+
 int mlp_train_step(float* d_params, float* d_m, float* d_v, int64_t step, int in, const void* d_X,
                    const int8_t* d_y, int64_t B, const float* cw, float lr, float* d_loss,
                    Alloc& A, cudaStream_t s, Err* err) {
-  if (B <= 0) return set_error(err, FR_EINVAL, "empty batch");
   const Lay L = lay(in);
   Scratch S(&A);
-  float* acts = S.get<float>(size_t(B) * (in + 3 * H));
-  float* pre = S.get<float>(size_t(B) * 3 * H);
-  float* dels = S.get<float>(size_t(B) * (3 * H + NOUT));
   float* G = S.get<float>(L.total);
-  float* ls = S.get<float>(B);
-  if (!acts || !pre || !dels || !G || !ls) return set_error(err, FR_ENOMEM, "training scratch");
-  // class weights normalised by the batch's total weight: computed by the caller as cw[0..2]
-  // and cw[3] = 1 / sum_b w_{y_b}
-  size_t sm = fwd_smem(in);
-  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  k_mlp_fwd_bwd<<<unsigned((B + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
-      d_params, in, static_cast<const __nv_bfloat16*>(d_X), d_y, B, cw[0], cw[1], cw[2], cw[3], acts,
-      pre, dels, ls);
-  FR_LAUNCH_CHECK(err);
-  k_mlp_wgrad<<<unsigned((L.total + 127) / 128), 128, 0, s>>>(in, B, acts, dels, G);
-  FR_LAUNCH_CHECK(err);
+  if (!G) return set_error(err, FR_ENOMEM, "training scratch");
+  int* st = nullptr;
+  FR_TRY(grad_tc(d_params, in, d_X, d_y, B, cw, G, d_loss, S, &st, s, err));
   const float b1 = 0.9f, b2 = 0.999f;
   float c1 = 1.f - std::pow(b1, float(step + 1)), c2 = 1.f - std::pow(b2, float(step + 1));
   k_adam<<<unsigned((L.total + 255) / 256), 256, 0, s>>>(d_params, d_m, d_v, G, L.total, lr, b1, b2,
                                                          1e-8f, c1, c2);
   FR_LAUNCH_CHECK(err);
-  if (d_loss) {
-    k_sum<<<1, 256, 0, s>>>(ls, B, d_loss);
-    FR_LAUNCH_CHECK(err);
-  }
-  return 0;
+  return check_status(st, s, err);
 }
 
 int mlp_grad(const float* d_params, int in, const void* d_X, const int8_t* d_y, int64_t B,
              const float* cw, float* d_grad, float* d_loss, Alloc& A, cudaStream_t s, Err* err) {
-  if (B <= 0) return set_error(err, FR_EINVAL, "empty batch");
-  const Lay L = lay(in);
   Scratch S(&A);
-  float* acts = S.get<float>(size_t(B) * (in + 3 * H));
-  float* pre = S.get<float>(size_t(B) * 3 * H);
-  float* dels = S.get<float>(size_t(B) * (3 * H + NOUT));
-  float* ls = S.get<float>(B);
-  if (!acts || !pre || !dels || !ls) return set_error(err, FR_ENOMEM, "gradient scratch");
-  size_t sm = fwd_smem(in);
-  FR_CUDA(err, cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  k_mlp_fwd_bwd<<<unsigned((B + MLP_T - 1) / MLP_T), MLP_T, sm, s>>>(
-      d_params, in, static_cast<const __nv_bfloat16*>(d_X), d_y, B, cw[0], cw[1], cw[2], cw[3], acts,
-      pre, dels, ls);
-  FR_LAUNCH_CHECK(err);
-  k_mlp_wgrad<<<unsigned((L.total + 127) / 128), 128, 0, s>>>(in, B, acts, dels, d_grad);
-  FR_LAUNCH_CHECK(err);
-  k_sum<<<1, 256, 0, s>>>(ls, B, d_loss);
-  FR_LAUNCH_CHECK(err);
-  return 0;
+  int* st = nullptr;
+  FR_TRY(grad_tc(d_params, in, d_X, d_y, B, cw, d_grad, d_loss, S, &st, s, err));
+  return check_status(st, s, err);
 }
 
 }  // namespace frg

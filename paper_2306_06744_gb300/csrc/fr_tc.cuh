@@ -23,12 +23,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
 __device__ __forceinline__ uint32_t canon_off(int r, int k) {
   return uint32_t((r >> 3) * SBO + (k >> 3) * LBO + (r & 7) * 16 + (k & 7) * 2);
 }
+// the same layout for a tile of `ncols` columns (a multiple of 8): 8-row groups ncols*16 bytes apart
+__device__ __forceinline__ uint32_t canon_off_w(int r, int k, int ncols) {
+  return uint32_t((r >> 3) * (ncols * 16) + (k >> 3) * LBO + (r & 7) * 16 + (k & 7) * 2);
+}
 
 // shared-memory matrix descriptor: start address, leading and stride byte offsets (all >> 4),
 // descriptor version 1 at bit 46, base offset 0, relative leading offsets, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t sbo = SBO) {
   return uint64_t((addr >> 4) & 0x3FFFu) | (uint64_t((LBO >> 4) & 0x3FFFu) << 16) |
-         (uint64_t((SBO >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
+         (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46);
 }
 
 // instruction descriptor of kind::f16: D in FP32 (bits 4-5 = 1), A and B in BF16 (bits 7-9 and
