@@ -188,9 +188,41 @@ def bench_forward(n: int = 2_000_000, n_in: int = 55, reps: int = 10, seed: int 
                 gbs=n * (2 * n_in + 12 + 1) / t / 1e9)
 
 
+def bench_train(batch: int = 65536, n_in: int = 55, reps: int = 20, seed: int = 1) -> dict:
+    """Times one tensor-core training step (fr_mlp_train_step: gradient of a batch and the Adam
+    update, including the call's status check) on seeded synthetic features and labels."""
+    import torch
+    npar = fr.mlp_param_count(n_in)
+    P = torch.from_numpy(((W.random_uniform(npar, seed) - 0.5) * 0.5).astype(np.float32)).cuda()
+    m, v = torch.zeros_like(P), torch.zeros_like(P)
+    X = torch.from_numpy(((W.random_uniform(batch * n_in, seed + 1) - 0.5) * 6).astype(np.float32))
+    X = X.reshape(batch, n_in).cuda().to(torch.bfloat16)
+    y = torch.from_numpy((np.floor(W.random_uniform(batch, seed + 2) * 3) - 1).astype(np.int8)).cuda()
+    cw = [1.5, 0.5, 2.0]
+    fr.mlp_train_step(P, m, v, 0, X, y, cw, 1e-3)
+    ms = []
+    for k in range(1, reps + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fr.mlp_train_step(P, m, v, k, X, y, cw, 1e-3)
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = float(np.median(ms)) * 1e-3
+    macs = n_in * 64 + 2 * 64 * 64 + 64 * 3
+    # forward, backward-data, weight gradients and the recomputed pre-activations: ~4 passes
+    return dict(batch=batch, in_dim=n_in, ms=t * 1e3, samples_per_s=batch / t,
+                tflops_4pass=4 * 2.0 * macs * batch / t / 1e12)
+
+
 if __name__ == "__main__":
     import json
     import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "--bench-train":
+        b = int(sys.argv[2]) if len(sys.argv) > 2 else 65536
+        n_in = int(sys.argv[3]) if len(sys.argv) > 3 else 55
+        print(json.dumps(bench_train(b, n_in)))
+        sys.exit(0)
     if len(sys.argv) > 1 and sys.argv[1] == "--bench-forward":
         n = int(sys.argv[2]) if len(sys.argv) > 2 else 2_000_000
         n_in = int(sys.argv[3]) if len(sys.argv) > 3 else 55
