@@ -134,7 +134,11 @@ int fr_run(fr_mesh* m, int nsteps, fr_step_stats* step_stats, fr_adapt_stats* ad
 /* One adaptation (Sec. 4.1 procedure, then 2:1 balance, old->new mapping, solution transfer
    Sec. 4.2, connectivity Sec. 3.3).  flags: device int8[M] in {-1,0,1} borrowed for the call, or
    NULL to evaluate the configured indicator.  Refinement at Dmax and coarsening at Dbase are
-   ignored; a leaf changes at most one level before balancing.  stats may be NULL. */
+   ignored; a leaf changes at most one level before balancing.  stats may be NULL.  The whole
+   adaptation is issued against device-side counts with one host synchronisation at its end when
+   2^dim * M <= 2^20 (a balance pass generating more than 4096 octants is then finished with exact
+   sizes, one synchronisation per pass); larger meshes synchronise once per balance pass.
+   FR_EINVAL if the new tree fails a consistency check; FR_ETIMEOUT from the learned indicator. */
 int fr_adapt(fr_mesh* m, const int8_t* dev_flags, fr_adapt_stats* stats);
 
 /* Indicator flags of the current state (not applied).  host flags int8[M], eta double[M] (may be
@@ -151,7 +155,8 @@ int fr_norms(fr_mesh* m, fr_norms_out* out);
 int fr_get_leaves(fr_mesh* m, uint64_t* host_keys, int64_t cap, int64_t* M);
 int fr_get_state(fr_mesh* m, double* host_u, int64_t cap);
 /* Replaces tree and state (keys must form a complete, sorted, 2:1-balanced linear tree with
-   depths in [Dbase, Dmax]; FR_EINVAL otherwise). */
+   depths in [Dbase, Dmax]; FR_EINVAL otherwise, and the mesh is left as it was).  The copies,
+   the validation and the connectivity take one host synchronisation. */
 int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double* host_u);
 /* Connectivity tables, host arrays of M*2*dim entries. */
 int fr_get_conn(fr_mesh* m, int32_t* host_nbr, int8_t* host_ftype, int8_t* host_slot, int64_t cap);
