@@ -87,12 +87,15 @@ __global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M_ub, con
 
 template <int DIM>
 __global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
-                             int64_t M_ub, const int64_t* __restrict__ d_M, const int64_t* __restrict__ off,
+                             int64_t M_ub, const int64_t* __restrict__ d_M, const Offs O,
                              int32_t* __restrict__ conf, int32_t* __restrict__ hang, int32_t* __restrict__ hcon) {
   pdl_wait_then_release();
+  int64_t grand;
+  const int64_t base = offs_base(O, int64_t(blockIdx.x) * blockDim.x, &grand);
   int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M_ub || (d_M && e >= *d_M)) return;
-  int64_t a = off[e] & 0xFFFFFFFFll, b = off[e] >> 32;
+  const int64_t off = O.offs[e] + base;  // packed: conforming count low, hanging count high
+  int64_t a = off & 0xFFFFFFFFll, b = off >> 32;
 #pragma unroll
   for (int f = 0; f < 2 * DIM; ++f) {
     int8_t t = ftype[e * 2 * DIM + f];
@@ -148,7 +151,8 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   else
     launch_dependent(k_face_count<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts64(cnt, off, n_ub, d_faces, Sc, s, err));
+  Offs O;
+  FR_TRY(scan_counts64_local(cnt, off, n_ub, d_faces, Sc, s, err, &O));
   // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
   // bound so the writes need no synchronisation
   FR_TRY(m->conf.ensure(m->A, size_t(n_ub) * m->dim));
@@ -156,10 +160,10 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   FR_TRY(hcon.ensure(m->A, size_t(n_ub) * m->nfc * 4));
   if (m->dim == 2)
     launch_dependent(k_face_write<2>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p),
-                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, static_cast<const int64_t*>(off), m->conf.p, m->hang.p, hcon.p);
+                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, O, m->conf.p, m->hang.p, hcon.p);
   else
     launch_dependent(k_face_write<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p),
-                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, static_cast<const int64_t*>(off), m->conf.p, m->hang.p, hcon.p);
+                     static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, O, m->conf.p, m->hang.p, hcon.p);
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -271,6 +271,58 @@ struct Scratch {
 // Primitives (fr_prim.cu)
 // ---------------------------------------------------------------------------------------------
 // exclusive scan of int32 counts into int64 offsets; the total goes to *d_total (device)
+// Exclusive offsets produced by a scan: global (sums == nullptr, total already stored), or local
+// to tiles of SCAN_TILE_ITEMS items with the tile totals in sums[nb]; a consumer kernel then adds
+// its tile's base itself (offs_base) and its block 0 stores the grand total to *total, which saves
+// the scan's second launch.
+constexpr int64_t SCAN_TILE_ITEMS = 2048;
+struct Offs {
+  const int64_t* offs;
+  const int64_t* sums;
+  int64_t nb;
+  int64_t* total;
+};
+// Block-wide (every thread of the block calls it; blockDim a power of two <= 256; the block's
+// items, the first of which is i0, lie in one tile): the base of the block's tile, and the grand
+// total in *grand; block 0 stores the total.
+__device__ __forceinline__ int64_t offs_base(const Offs& O, int64_t i0, int64_t* grand) {
+  __shared__ int64_t red[256];
+  if (!O.sums) {
+    *grand = 0;
+    return 0;
+  }
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int64_t tile = i0 / SCAN_TILE_ITEMS;
+  int64_t a = 0, b = 0;
+  for (int64_t k = t; k < O.nb; k += nt) {
+    const int64_t v = O.sums[k];
+    b += v;
+    if (k < tile) a += v;
+  }
+  red[t] = a;
+  __syncthreads();
+  for (int st = nt / 2; st > 0; st >>= 1) {
+    if (t < st) red[t] += red[t + st];
+    __syncthreads();
+  }
+  const int64_t base = red[0];
+  __syncthreads();
+  red[t] = b;
+  __syncthreads();
+  for (int st = nt / 2; st > 0; st >>= 1) {
+    if (t < st) red[t] += red[t + st];
+    __syncthreads();
+  }
+  *grand = red[0];
+  if (blockIdx.x == 0 && t == 0) *O.total = red[0];
+  __syncthreads();
+  return base;
+}
+// scan whose second pass is left to the consumer when the input spans at most 256 tiles
+int scan_counts_local(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                      cudaStream_t s, Err* err, Offs* O);
+int scan_counts64_local(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                        cudaStream_t s, Err* err, Offs* O);
 int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
                 cudaStream_t s, Err* err);
 int scan_counts64(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,

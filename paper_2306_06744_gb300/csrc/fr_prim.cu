@@ -240,6 +240,31 @@ static int scan_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_tota
   return 0;
 }
 
+template <class TIn>
+static int scan_local_impl(const TIn* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                           cudaStream_t s, Err* err, Offs* O) {
+  static_assert(SCAN_TILE == SCAN_TILE_ITEMS, "tile size");
+  const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (n <= 0 || nb == 1 || nb > SCAN_PREFIX_MAX) {
+    *O = Offs{d_out, nullptr, 0, d_total};
+    return scan_impl<TIn>(d_in, d_out, n, d_total, S, s, err);
+  }
+  int64_t* sums = S.get<int64_t>(nb);
+  if (!sums) return set_error(err, FR_ENOMEM, "scan scratch");
+  launch_dependent(k_scan_tile<TIn>, unsigned(nb), SCAN_T, s, d_in, d_out, n, sums);
+  FR_LAUNCH_CHECK(err);
+  *O = Offs{d_out, sums, nb, d_total};
+  return 0;
+}
+int scan_counts_local(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                      cudaStream_t s, Err* err, Offs* O) {
+  return scan_local_impl<int32_t>(d_in, d_out, n, d_total, S, s, err, O);
+}
+int scan_counts64_local(const int64_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
+                        cudaStream_t s, Err* err, Offs* O) {
+  return scan_local_impl<int64_t>(d_in, d_out, n, d_total, S, s, err, O);
+}
+
 int scan_counts(const int32_t* d_in, int64_t* d_out, int64_t n, int64_t* d_total, Scratch& S,
                 cudaStream_t s, Err* err) {
   return scan_impl<int32_t>(d_in, d_out, n, d_total, S, s, err);

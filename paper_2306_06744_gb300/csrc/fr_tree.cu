@@ -99,13 +99,15 @@ __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __res
 
 template <int DIM>
 __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __restrict__ act,
-                             const int64_t* __restrict__ offs, int64_t n, KG g,
-                             uint64_t* __restrict__ out, unsigned long long* stats) {
+                             const Offs O, int64_t n, KG g, uint64_t* __restrict__ out,
+                             unsigned long long* stats) {
   pdl_wait_then_release();
+  int64_t grand;
+  const int64_t base = offs_base(O, int64_t(blockIdx.x) * blockDim.x, &grand);
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   uint64_t key = k[i];
-  int64_t o = offs[i];
+  int64_t o = O.offs[i] + base;
   switch (act[i]) {
     case 0: out[o] = key; break;
     case 1:
@@ -195,15 +197,20 @@ __global__ void k_bal_count(const uint64_t* __restrict__ k, const int64_t* __res
 }
 
 template <int DIM>
-__global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
-                          int64_t n_ub, KG g, int D, const int64_t* __restrict__ offs,
+__global__ void k_bal_gen(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl,
+                          int64_t n_ub, KG g, int D, const Offs O,
                           uint64_t* __restrict__ out, int64_t cap) {
   pdl_wait_then_release();
   constexpr int LPL = BalLanes<DIM>::value;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = gt / LPL;
   const int o = int(gt % LPL);
-  const int64_t n = bal_nS(ctl, cap) > 0 ? ctl[CTL_N] : 0;
+  // the pass's octant count: from the tile totals (block 0 then stores it in ctl[CTL_G]) or,
+  // after a full scan, from ctl[CTL_G]
+  int64_t grand;
+  const int64_t base = offs_base(O, int64_t(blockIdx.x) * (blockDim.x / LPL), &grand);
+  const int64_t G = O.sums ? grand : ctl[CTL_G];
+  const int64_t n = (ctl[CTL_OVER] == 0 && G > 0 && G <= cap) ? ctl[CTL_N] : 0;
   uint32_t N[3];
   int dA = 0;
   const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA) : 0;
@@ -215,7 +222,7 @@ __global__ void k_bal_gen(const uint64_t* __restrict__ k, const int64_t* __restr
     if (o >= w) incl += y;
   }
   if (c == 0) return;
-  int64_t q = offs[i] + (incl - c);
+  int64_t q = O.offs[i] + base + (incl - c);
   const uint64_t rawN = interleave<DIM>(N);
   for (int l = dA + 1; l <= D - 1; ++l) {
     const uint64_t span = vol_raw<DIM>(g, l - 1);
@@ -331,14 +338,16 @@ template <int DIM>
 __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl,
                               int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap, KG g,
                               bool linearised, const int32_t* __restrict__ cnt,
-                              const int64_t* __restrict__ lo, const int64_t* __restrict__ offs,
+                              const int64_t* __restrict__ lo, const Offs O,
                               uint64_t* __restrict__ out) {
   pdl_wait_then_release();
+  int64_t grand;
+  const int64_t base = offs_base(O, int64_t(blockIdx.x) * blockDim.x, &grand);
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n_ub) return;
   const int c = cnt[i];
   if (c == 0) return;
-  int64_t o = offs[i], l = lo[i];
+  int64_t o = O.offs[i] + base, l = lo[i];
   if (l < 0) {
     out[o] = k[i];
     return;
@@ -654,8 +663,9 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt,
                                       d_ctl, d_bad)));
   FR_LAUNCH_CHECK(err);
-  FR_TRY(scan_counts(cnt, offs, n, d_ctl + CTL_N, S, s, err));
-  DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, offs, n, g, out.p,
+  Offs O;
+  FR_TRY(scan_counts_local(cnt, offs, n, d_ctl + CTL_N, S, s, err, &O));
+  DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, O, n, g, out.p,
                                                                reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF))));
   FR_LAUNCH_CHECK(err);
   return 0;
@@ -675,13 +685,14 @@ static int read_ctl(const int64_t* d_ctl, int64_t* h_ctl, cudaStream_t s, Err* e
 // pass (small sort only).  `exact_G` >= 0: the host knows the generated count (sizes from it).
 static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<uint64_t>& out,
                         Buf<uint64_t>& gen, Buf<uint64_t>& tmp, int64_t* d_ctl, int64_t n_ub,
-                        int64_t exact_G, int64_t cap, const int32_t* cnt, const int64_t* offs,
-                        Alloc& A, cudaStream_t s, Err* err) {
+                        int64_t exact_G, int64_t cap, const Offs& Ocnt, Alloc& A, cudaStream_t s,
+                        Err* err) {
   Scratch S(&A);
   const int64_t G_ub = exact_G >= 0 ? exact_G : cap;
   FR_TRY(gen.ensure(A, size_t(G_ub)));
   FR_TRY(out.ensure(A, size_t(n_ub + G_ub)));
-  DIM_DISPATCH(dim, (launch_dependent(k_bal_gen<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D, offs, gen.p, cap)));
+  DIM_DISPATCH(dim, (launch_dependent(k_bal_gen<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D,
+                                      Ocnt, gen.p, cap)));
   FR_LAUNCH_CHECK(err);
   if (exact_G < 0 || exact_G <= SMALL_SORT_MAX) {
     launch_dependent(k_sort_small, 1, 1024, s, gen.p, d_ctl, cap, D);
@@ -715,9 +726,10 @@ static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<ui
                                       lin_first, cnt2, lo)));
   FR_LAUNCH_CHECK(err);
   // the merged tree has at most n + G leaves; its count replaces ctl[CTL_N] on the device
-  FR_TRY(scan_counts(cnt2, offs2, n_ub, d_ctl + CTL_N, S, s, err));
+  Offs Om;
+  FR_TRY(scan_counts_local(cnt2, offs2, n_ub, d_ctl + CTL_N, S, s, err, &Om));
   DIM_DISPATCH(dim, (launch_dependent(k_merge_write<D_>, nblk(n_ub), TB, s, keys.p, d_ctl, n_ub, src, cap, g,
-                                      lin_first, cnt2, lo, offs2, out.p)));
+                                      lin_first, cnt2, lo, Om, out.p)));
   FR_LAUNCH_CHECK(err);
   Buf<uint64_t> t = keys;  // the merged tree becomes the tree
   keys = out;
@@ -753,7 +765,9 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
     const int64_t n = h_ctl[CTL_N], G = h_ctl[CTL_G];
     n_ub = n;
     if (G == 0) continue;
-    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, cnt, offs, A, s, err))) break;
+    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, Offs{offs, nullptr, 0, d_ctl + CTL_G},
+                           A, s, err)))
+      break;
     n_ub = n + G;
     known = false;
   }
@@ -780,9 +794,9 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
     DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g, D, cnt)));
     ++launch_counter();
     if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    if ((rc = scan_counts(cnt, offs, nb, d_ctl + CTL_G, S, s, err))) break;
-    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, nb, -1, SMALL_SORT_MAX, cnt, offs, A, s, err)))
-      break;
+    Offs O;
+    if ((rc = scan_counts_local(cnt, offs, nb, d_ctl + CTL_G, S, s, err, &O))) break;
+    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, nb, -1, SMALL_SORT_MAX, O, A, s, err))) break;
     *n_ub = nb + SMALL_SORT_MAX;
   }
   gen.release(A);
