@@ -376,11 +376,13 @@ def main():
     except Exception:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    tr = _traffic_from_profiles("k_stage")
-    # DRAM bytes per launch from the ncu capture, scaled to this run's mean launch size
+    kname = "k_stage<%d,%d>" % (dim, p + 1)
+    tr = _traffic_from_profiles(kname)
+    # DRAM bytes per launch from the ncu capture of this kernel instance, scaled to this run's
+    # mean launch size
     traffic = (tr["bytes"] * (prof["stage_points"] / max(1, prof["stage_launches"])) / tr["points"]
                if tr else None)
-    roofline = {"kernel": "k_stage<2,4> (element stage)", "bound": "alu",
+    roofline = {"kernel": kname + " (element stage)", "bound": "alu",
                 "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (recipe unit counts "
