@@ -258,7 +258,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.trace_out = traces ? m->trace.p : nullptr;
   S.M = m->M;
   S.g = m->g;
-  S.L = m->cfg.L;
+  S.twoL = 2.0 / m->cfg.L;
   S.gamma = m->cfg.gamma;
   S.a = a;
   S.b = b;

@@ -17,7 +17,9 @@ namespace frg {
 template <class T>
 struct OpsT {
   T Dt[NPMAX][NPMAX];
-  T gL[NPMAX], gR[NPMAX], lm[NPMAX], lp[NPMAX];
+  // gLh, gRh: half the correction slopes g'_L, g'_R at the solution points, because the
+  // interface kernel stores twice the common flux (exact scalings by 2 and 1/2)
+  T gLh[NPMAX], gRh[NPMAX], lm[NPMAX], lp[NPMAX];
   T I[2][NPMAX][NPMAX];
   T P[2][NPMAX][NPMAX];
 };
@@ -35,8 +37,8 @@ OpsT<T> make_ops_t(const DevOps& o) {
   OpsT<T> r{};
   T* tag = nullptr;
   for (int i = 0; i < NPMAX; ++i) {
-    r.gL[i] = host_conv(o.gL[i], tag);
-    r.gR[i] = host_conv(o.gR[i], tag);
+    r.gLh[i] = host_conv(0.5 * o.gL[i], tag);
+    r.gRh[i] = host_conv(0.5 * o.gR[i], tag);
     r.lm[i] = host_conv(o.lm[i], tag);
     r.lp[i] = host_conv(o.lp[i], tag);
     for (int j = 0; j < NPMAX; ++j) {
@@ -90,11 +92,13 @@ __device__ __forceinline__ void pt_split(int i, int axis, int* q, int* ia) {
   }
 }
 
-// Rusanov common flux along +axis between the minus-side state qL and the plus-side qR, with
-// lambda = max(|u_n| + c) of the two states (Sec. 4.3).
+// Twice the Rusanov common flux along +axis between the minus-side state qL and the plus-side
+// qR, F2 = f(qL) + f(qR) - lambda (qR - qL) with lambda = max(|u_n| + c) of the two states
+// (Sec. 4.3); the factor 1/2 is carried by the correction slopes.  ngmh = -(gamma - 1)/2, so
+// that p = (gamma - 1) E + ngmh |m|^2 / rho.
 template <int DIM, class T>
-__device__ __forceinline__ void rusanov_t(const T* qL, const T* qR, int axis, T gam, T gm1, T half,
-                                          T* F) {
+__device__ __forceinline__ void rusanov2_t(const T* qL, const T* qR, int axis, T gam, T gm1, T ngmh,
+                                           T* F2) {
   constexpr int NV = DIM + 2;
   T rL = rcp_t(qL[0]), rR = rcp_t(qR[0]);
   T m2L = qL[1] * qL[1], m2R = qR[1] * qR[1];
@@ -103,8 +107,8 @@ __device__ __forceinline__ void rusanov_t(const T* qL, const T* qR, int axis, T 
     m2L = fma_t(qL[1 + b], qL[1 + b], m2L);
     m2R = fma_t(qR[1 + b], qR[1 + b], m2R);
   }
-  T pL = gm1 * (qL[NV - 1] - half * m2L * rL);
-  T pR = gm1 * (qR[NV - 1] - half * m2R * rR);
+  T pL = fma_t(ngmh, m2L * rL, gm1 * qL[NV - 1]);
+  T pR = fma_t(ngmh, m2R * rR, gm1 * qR[NV - 1]);
   // normal momenta, selected with unrolled predicates so the state stays in registers
   T mnL = qL[1], mnR = qR[1];
 #pragma unroll
@@ -116,7 +120,6 @@ __device__ __forceinline__ void rusanov_t(const T* qL, const T* qR, int axis, T 
   T vL = mnL * rL, vR = mnR * rR;
   T cL = sqrt_t(gam * pL * rL), cR = sqrt_t(gam * pR * rR);
   T lam = fmax_t(fabs_t(vL) + cL, fabs_t(vR) + cR);
-  T hl = half * lam;
   T fL[NV], fR[NV];
   fL[0] = mnL;
   fR[0] = mnR;
@@ -129,7 +132,7 @@ __device__ __forceinline__ void rusanov_t(const T* qL, const T* qR, int axis, T 
   fL[NV - 1] = (qL[NV - 1] + pL) * vL;
   fR[NV - 1] = (qR[NV - 1] + pR) * vR;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) F[v] = half * (fL[v] + fR[v]) - hl * (qR[v] - qL[v]);
+  for (int v = 0; v < NV; ++v) F2[v] = fma_t(lam, qL[v] - qR[v], fL[v] + fR[v]);
 }
 
 template <class T>
@@ -205,7 +208,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   __shared__ T sF[FPB][NSUB][NV][NF];
   const T* trace = static_cast<const T*>(A.trace);
   T* fcomm = static_cast<T*>(A.fcomm);
-  const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
+  const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), ngmh = cst<T>(-0.5 * (A.gamma - 1.0));
   const int tid = threadIdx.x;
   // the face lists and neighbour tables are fixed during a time step: they are read while the
   // element kernel this one depends on drains; the traces it wrote are read after the wait
@@ -227,7 +230,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
       qL[v] = tL[v * NF];
       qR[v] = tR[v * NF];
     }
-    rusanov_t<DIM, T>(qL, qR, axis, gam, gm1, half, F);
+    rusanov2_t<DIM, T>(qL, qR, axis, gam, gm1, ngmh, F);
     T* fL = fcomm + ((e * NFC + 2 * axis + 1) * NV) * NF + q;
     T* fR = fcomm + ((nb * NFC + 2 * axis) * NV) * NF + q;
 #pragma unroll
@@ -276,9 +279,9 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
       uf[v] = trace[((ek * NFC + fk) * NV + v) * NF + q];
     }
     if (sidec)
-      rusanov_t<DIM, T>(uc, uf, axis, gam, gm1, half, F);
+      rusanov2_t<DIM, T>(uc, uf, axis, gam, gm1, ngmh, F);
     else
-      rusanov_t<DIM, T>(uf, uc, axis, gam, gm1, half, F);
+      rusanov2_t<DIM, T>(uf, uc, axis, gam, gm1, ngmh, F);
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       fcomm[((ek * NFC + fk) * NV + v) * NF + q] = F[v];
@@ -336,7 +339,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   __shared__ T su[EPB * EU];
   __shared__ T sfl[EPB * DIM * EU];
   __shared__ T sfc[EPB * EF];
-  __shared__ double sh2[EPB];
+  __shared__ double sh2[EPB];  // per element: c * (-2/h)
   const T* fcomm = static_cast<const T*>(A.fcomm);
   T* trace_out = static_cast<T*>(A.trace_out);
   const int tid = threadIdx.x;
@@ -345,13 +348,14 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   // the stage's input state and the keys come from earlier launches than the interface kernel
   // this one depends on: they are read while that kernel drains; the common fluxes after it
   for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
-  if (tid < ne) sh2[tid] = double(2ull << A.g.depth(A.keys[e0 + tid])) / A.L;  // 2/h
+  // c * (-2/h): 2^depth * (2/L) is exact, so this equals the rounded -2^(depth+1)/L times c
+  if (tid < ne) sh2[tid] = -A.c * (double(1ull << A.g.depth(A.keys[e0 + tid])) * A.twoL);
   pdl_wait_then_release();
   for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   __syncthreads();
   const int le = tid / N, i = tid % N;
   const bool act = le < ne;
-  const T gm1 = cst<T>(A.gamma - 1.0), half = cst<T>(0.5);
+  const T gm1 = cst<T>(A.gamma - 1.0), ngmh = cst<T>(-0.5 * (A.gamma - 1.0));
   RT outv[NV];
   if (act) {
     const T* q = su + le * EU;
@@ -363,17 +367,23 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       vel[b] = q[(1 + b) * N + i] * rinv;
       m2 = fma_t(q[(1 + b) * N + i], vel[b], m2);
     }
-    T p = gm1 * (E - half * m2);
+    T p = fma_t(ngmh, m2, gm1 * E);
     T Ep = E + p;
+    // momentum flux m_b v_a, symmetric in (a, b): each off-diagonal product is formed once
+    T mv[DIM][DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = a; b < DIM; ++b) {
+        mv[a][b] = q[(1 + b) * N + i] * vel[a];
+        mv[b][a] = mv[a][b];
+      }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       T* fa = sfl + (le * DIM + a) * EU;
       fa[i] = q[(1 + a) * N + i];
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T mv = q[(1 + b) * N + i] * vel[a];
-        fa[(1 + b) * N + i] = (a == b) ? mv + p : mv;
-      }
+      for (int b = 0; b < DIM; ++b) fa[(1 + b) * N + i] = (a == b) ? mv[a][b] + p : mv[a][b];
       fa[(NV - 1) * N + i] = Ep * vel[a];
     }
   }
@@ -390,27 +400,28 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       const T* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        T d = a == 0 ? ops.gR[ia] * Fp[v * NF] : fma_t(ops.gR[ia], Fp[v * NF], R[v]);
-        d = fma_t(ops.gL[ia], Fm[v * NF], d);
+        T d = a == 0 ? ops.gRh[ia] * Fp[v * NF] : fma_t(ops.gRh[ia], Fp[v * NF], R[v]);
+        d = fma_t(ops.gLh[ia], Fm[v * NF], d);
 #pragma unroll
         for (int j = 0; j < NP; ++j) d = fma_t(ops.Dt[ia][j], fa[v * N + line_pt<DIM, NP>(a, qf, j)], d);
         R[v] = d;
       }
     }
-    const double s2 = -sh2[le];
+    const double cs = sh2[le];
     const int64_t base = (e0 + le) * EU + i;
     if constexpr (!std::is_same<T, ff>::value) {
-      // FP64 combination (native FP64 and the mixed FP32 form)
-      const double cs = A.c * s2;
+      // FP64 combination (native FP64 and the mixed FP32 form); b = 1 (first stage) skips the
+      // product, which is exact there
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double o = fma(cs, Ar<T>::to_d(R[v]), A.b * A.us[base + v * N]);
+        const double us = A.us[base + v * N];
+        double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? us : A.b * us);
         if (A.a != 0.0) o = fma(A.a, A.un[base + v * N], o);
         outv[v] = o;
       }
     } else {
       // double-word combination
-      const ff bb = ff_from_double(A.b), cc = ff_from_double(A.c * s2), aa = ff_from_double(A.a);
+      const ff bb = ff_from_double(A.b), cc = ff_from_double(cs), aa = ff_from_double(A.a);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         ff o = fma_t(bb, su[le * EU + v * N + i], cc * R[v]);

@@ -6,7 +6,7 @@ namespace frg {
 
 struct FaceArgs {
   const void* trace;      // [M][2dim][nv][Nf] traces of the current stage state (arithmetic type)
-  void* fcomm;            // [M][2dim][nv][Nf] common flux along +axis (arithmetic type)
+  void* fcomm;            // [M][2dim][nv][Nf] twice the common flux along +axis (arithmetic type)
   const int32_t* nbr;     // [M][2dim]
   const int32_t* conf;    // conforming faces: (minus element << 2) | axis
   const int32_t* hang;    // hanging faces: (coarse element << 3) | coarse face
@@ -19,12 +19,12 @@ struct StageArgs {
   const uint64_t* keys;
   const double* us;     // stage state
   const double* un;     // state at the start of the step (read only when a != 0)
-  const void* fcomm;    // common fluxes in the arithmetic type
+  const void* fcomm;    // twice the common fluxes, in the arithmetic type
   double* out;          // a*un + b*us + c*R (may alias us or un element-wise)
   void* trace_out;      // traces of out in the arithmetic type, or null
   int64_t M;
   KG g;
-  double L, gamma, a, b, c;
+  double twoL, gamma, a, b, c;  // twoL = 2 / L
 };
 
 struct Mesh;  // defined in fr_api.cu
