@@ -289,10 +289,11 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
     }
   }
   __syncthreads();
-  if (act && s == 0) {
-    const int q0 = q % NP;
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
+  // back-projection onto the coarse face: its NV*NF outputs are spread over all PER threads of
+  // the face (an idle lane costs the FP64 unit as much as a busy one)
+  if (act) {
+    for (int o = r; o < NV * NF; o += PER) {
+      const int v = o / NF, qc = o % NF, q0 = qc % NP;
       T acc = zero_t<T>();
 #pragma unroll
       for (int sp = 0; sp < NSUB; ++sp) {
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
 #pragma unroll
           for (int i0 = 0; i0 < NP; ++i0) acc = fma_t(ops.P[h0][q0][i0], sF[lf][sp][v][i0], acc);
         } else {
-          const int q1 = q / NP, h1 = sp >> 1;
+          const int q1 = qc / NP, h1 = sp >> 1;
 #pragma unroll
           for (int i1 = 0; i1 < NP; ++i1) {
             T a1 = zero_t<T>();
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
           }
         }
       }
-      fcomm[((ec * NFC + fc) * NV + v) * NF + q] = acc;
+      fcomm[((ec * NFC + fc) * NV + v) * NF + qc] = acc;
     }
   }
 }
