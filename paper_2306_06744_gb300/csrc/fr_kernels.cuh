@@ -347,12 +347,11 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
   const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
   // the stage's input state and the keys come from earlier launches than the interface kernel
-  // this one depends on: they are read while that kernel drains; the common fluxes after it
+  // this one depends on, so they are read, and the pointwise fluxes formed from them, while that
+  // kernel drains; the common fluxes are read after it
   for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
   // c * (-2/h): 2^depth * (2/L) is exact, so this equals the rounded -2^(depth+1)/L times c
   if (tid < ne) sh2[tid] = -A.c * (double(1ull << A.g.depth(A.keys[e0 + tid])) * A.twoL);
-  pdl_wait_then_release();
-  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   __syncthreads();
   const int le = tid / N, i = tid % N;
   const bool act = le < ne;
@@ -388,6 +387,8 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       fa[(NV - 1) * N + i] = Ep * vel[a];
     }
   }
+  pdl_wait_then_release();
+  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   __syncthreads();
   if (act) {
     // the per-axis sums are accumulated straight into R (one FMA chain per variable)
@@ -415,7 +416,9 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       // product, which is exact there
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double us = A.us[base + v * N];
+        // u_s: the staged copy when it is exact (FP64), else the FP64 state in memory
+        const double us = std::is_same<T, double>::value ? Ar<T>::to_d(su[le * EU + v * N + i])
+                                                         : A.us[base + v * N];
         double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? us : A.b * us);
         if (A.a != 0.0) o = fma(A.a, A.un[base + v * N], o);
         outv[v] = o;
