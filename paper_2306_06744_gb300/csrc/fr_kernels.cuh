@@ -387,27 +387,38 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       fa[(NV - 1) * N + i] = Ep * vel[a];
     }
   }
-  pdl_wait_then_release();
-  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
   __syncthreads();
+  // volume part of the folded derivative, sum_a sum_j Dt_ij f_j, also before the wait: one FMA
+  // chain per variable, the correction terms are added once the common fluxes are in
+  T R[NV];
   if (act) {
-    // the per-axis sums are accumulated straight into R (one FMA chain per variable)
-    T R[NV];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
       int qf, ia;
       pt_split<DIM, NP>(i, a, &qf, &ia);
       const T* fa = sfl + (le * DIM + a) * EU;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        T d = a == 0 ? ops.Dt[ia][0] * fa[v * N + line_pt<DIM, NP>(a, qf, 0)]
+                     : fma_t(ops.Dt[ia][0], fa[v * N + line_pt<DIM, NP>(a, qf, 0)], R[v]);
+#pragma unroll
+        for (int j = 1; j < NP; ++j) d = fma_t(ops.Dt[ia][j], fa[v * N + line_pt<DIM, NP>(a, qf, j)], d);
+        R[v] = d;
+      }
+    }
+  }
+  pdl_wait_then_release();
+  for (int k = tid; k < ne * EF; k += blockDim.x) sfc[k] = fcomm[e0 * EF + k];
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      int qf, ia;
+      pt_split<DIM, NP>(i, a, &qf, &ia);
       const T* Fm = sfc + le * EF + (2 * a) * NV * NF + qf;
       const T* Fp = sfc + le * EF + (2 * a + 1) * NV * NF + qf;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        T d = a == 0 ? ops.gRh[ia] * Fp[v * NF] : fma_t(ops.gRh[ia], Fp[v * NF], R[v]);
-        d = fma_t(ops.gLh[ia], Fm[v * NF], d);
-#pragma unroll
-        for (int j = 0; j < NP; ++j) d = fma_t(ops.Dt[ia][j], fa[v * N + line_pt<DIM, NP>(a, qf, j)], d);
-        R[v] = d;
-      }
+      for (int v = 0; v < NV; ++v) R[v] = fma_t(ops.gLh[ia], Fm[v * NF], fma_t(ops.gRh[ia], Fp[v * NF], R[v]));
     }
     const double cs = sh2[le];
     const int64_t base = (e0 + le) * EU + i;
