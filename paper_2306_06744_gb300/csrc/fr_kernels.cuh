@@ -100,7 +100,9 @@ template <int DIM, class T>
 __device__ __forceinline__ void rusanov2_t(const T* qL, const T* qR, int axis, T gam, T gm1, T ngmh,
                                            T* F2) {
   constexpr int NV = DIM + 2;
-  T rL = rcp_t(qL[0]), rR = rcp_t(qR[0]);
+  // both reciprocal densities from one reciprocal: 1/rho_L = rho_R / (rho_L rho_R), and so on
+  const T rLR = rcp_t(qL[0] * qR[0]);
+  T rL = qR[0] * rLR, rR = qL[0] * rLR;
   T m2L = qL[1] * qL[1], m2R = qR[1] * qR[1];
 #pragma unroll
   for (int b = 1; b < DIM; ++b) {
