@@ -175,6 +175,7 @@ def run_reference(args):
             "data": "synthetic",
             "config": dict(_config_line(cfg), l2="n/a (CPU)"),
             "adaptation_pct": 100.0 * t_adapt / (t_steps + t_adapt),
+            "point_updates_per_s": value / nv,
             "l2_rho": o.norms()["l2_rho"], "M_final": o.M,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d of %d cycles of %s after %d warm-up cycles, %.1f s" %
@@ -486,6 +487,9 @@ def main():
             "config": dict(_config_line(cfg), l2="flushed between steps (512 MB write)",
                            parallelism="replicas" if world > 1 else "single GPU"),
             "adaptation_pct": 100.0 * t_adapt / (t_step + t_adapt),
+            # solution-point updates per second (DOF-updates / conserved variables), the unit of
+            # the paper's throughput figures
+            "point_updates_per_s": value / nv,
             "l2_rho": norms["l2_rho"], "t_final": norms["t"], "M_final": mesh.M,
             "M_mean": sum(Ms) / len(Ms), "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
