@@ -75,6 +75,46 @@ cudaError_t launch_dependent(Kern kernel, unsigned grid, unsigned block, cudaStr
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// launch_dependent with dynamic shared memory (see residency_pad)
+template <class Kern, class... Args>
+cudaError_t launch_dependent_smem(Kern kernel, unsigned grid, unsigned block, size_t dyn_smem,
+                                  cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = dyn_smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
+// Unused dynamic shared memory that holds a kernel to at most max_warps resident warps per SM:
+// the smallest per-block footprint that no longer fits one block more than that; 0 where shared
+// memory already allows no more (or the attributes cannot be read).
+template <class Kern>
+size_t residency_pad(Kern kernel, int threads, int max_warps) {
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0, reserved = 0;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int blocks = max_warps / ((threads + 31) / 32);
+  if (blocks < 1) return 0;
+  const long need = long(smem_sm) / (blocks + 1) + 1;  // footprint above which blocks+1 do not fit
+  long pad = need - long(reserved) - long(fa.sharedSizeBytes);
+  if (pad <= 0) return 0;
+  pad = (pad + 127) / 128 * 128;
+  if (long(reserved) + long(fa.sharedSizeBytes) + pad > long(smem_sm) / blocks) return 0;
+  return size_t(pad);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Morton IDs (Sec. 2.2, Algorithm 1).  Bits are interleaved with the "magic number" bit spread
 // the paper mentions: spreading one coordinate's bits to every dim-th position by masked shifts.

@@ -531,6 +531,21 @@ int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t 
   return 0;
 }
 
+// Resident warps per SM allowed to the FP64 element kernel.  Its blocks are scheduled while the
+// interface kernel they wait for still runs (dependent launch) and hold their slots while they
+// wait; with the whole SM open to them (2D p = 3: 13 blocks of 4 warps, bounded by shared
+// memory) they leave that kernel too few warps.  Measured on the 2D p = 3 workload: 8, 9, 10, 11
+// and 16 resident blocks give +0.5, +0.7, +0.3, +0.15 and -1.4% against 13.  The other
+// arithmetic forms keep the full residency.
+constexpr int STAGE_F64_MAX_WARPS = 36;
+template <int DIM, int NP, class T>
+size_t stage_smem_pad() {
+  static const size_t pad = std::is_same<T, double>::value
+                                ? residency_pad(k_stage_t<DIM, NP, T>, Sz<DIM, NP>::BT, STAGE_F64_MAX_WARPS)
+                                : 0;
+  return pad;
+}
+
 template <class T>
 int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaStream_t s, Err* err) {
   if (A.M <= 0) return 0;
@@ -538,7 +553,8 @@ int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaS
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    unsigned nb = unsigned((A.M + SS::EPB - 1) / SS::EPB);
-                   if (launch_dependent(k_stage_t<DD, NN, T>, nb, SS::BT, s, A, ops) != cudaSuccess)
+                   if (launch_dependent_smem(k_stage_t<DD, NN, T>, nb, SS::BT, stage_smem_pad<DD, NN, T>(), s, A,
+                                             ops) != cudaSuccess)
                      return set_error(err, FR_ECUDA, "element kernel launch");
                  }));
   FR_LAUNCH_CHECK(err);
