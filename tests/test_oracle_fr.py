@@ -277,7 +277,8 @@ def test_entropy_wave_residual_is_weak_form_nodal_dg(dim, Dmax, p):
     # weak-form nodal DG residual written out here from its own definition:
     #   w_i (h/2) drho_i/dt = sum_j w_j D_ji f_j - l_i(+1) F*(+1) + l_i(-1) F*(-1)
     # per line of nodes (diagonal GL mass matrix; the quadrature is exact for these degree-2p
-    # integrands), with the Rusanov flux on the face traces, lambda = max(|v_n| + c) (C12).
+    # integrands), with the Rusanov flux on the face traces, lambda = max(|v_n| + c) of the two traces,
+    # point by point.
     cfg = W.config("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube")
     cfg.update(dim=dim, p=p, Dbase=Dmax, Dmax=Dmax, init_passes=0, indicator=2, dt=1e-3)
     L, g = cfg["L"], cfg["gamma"]
@@ -357,7 +358,8 @@ def paper_uniform_cfg(p, D, dt):
     """The paper's grid-refinement runs (Sec. 5.2): the vortex on a uniform periodic mesh of
     [-12.5, 12.5]^2 (here [0, 25]^2 with the centre in the middle), advected by u = (1, 1) for one
     period, t = 25; its Mach number 0.5 read as p_inf = rho_inf |u|^2 / (gamma Ma^2) with
-    |u| = sqrt(2) (reading C13).  dx = 25 / 2^D."""
+    |u| = sqrt(2) (the paper leaves the freestream pressure implicit; this reading reproduces its
+    tables, p_inf = 1 does not).  dx = 25 / 2^D."""
     L, g = 25.0, 1.4
     cfg = W.config("vortex2d_p2_small")
     cfg.update(p=p, L=L, Dbase=D, Dmax=D, init_passes=0, indicator=2, dt=dt, adapt_every=10 ** 9,
@@ -384,10 +386,11 @@ def test_paper_uniform_l2_error(p, dt, tol):
 
 @pytest.mark.skipif(not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS (about 5 minutes)")
 def test_paper_large_domain_adaptive_row():
-    # The paper's adaptive table for the large domain (Sec. 5.2, 100 wide per reading C22, one
-    # period t = 100): p = 1, Dmax 8 prints L2 4.64e-2 and 961 elements.  Its initial mesh is read
-    # top-down: uniform at Dmax, then Dmax - Dmin passes of the criterion (coarsening), then the
-    # exact state at the leaves.  (Bottom-up from Dmin, reading C14, leaves this mesh uniform at
+    # The paper's adaptive table for the large domain (Sec. 5.2; 100 wide: its element counts,
+    # 65536 at dx = 25/64, fix the width the text misprints; one period t = 100): p = 1, Dmax 8
+    # prints L2 4.64e-2 and 961 elements.  Its initial mesh is read top-down: uniform at Dmax,
+    # then Dmax - Dmin passes of the criterion (coarsening), then the exact state at the leaves.
+    # (Bottom-up from Dmin, as the library builds its initial mesh, leaves this mesh uniform at
     # Dmin: its 12.5-wide elements never hold more points inside radius 5 than beyond 6, and the
     # error comes out 2.8x larger; on the small domain both readings give the same run.)
     L, p, Dmax, n = 100.0, 1, 8, 2
