@@ -8,7 +8,8 @@ divergence, RK combination, traces) -- followed by one adaptation (indicator, re
 2:1 balance, mapping, transfer, connectivity).  K timed steps after W warm-up steps; L2 is flushed
 between steps (a 512 MB write outside the timed events).
 
-value  = DOF-updates/s = sum over time steps of M*N*nv / device time of the K cycles.
+value  = DOF-updates/s = sum over time steps of M*N*nv / device time of the K cycles
+         (point_updates_per_s: the same over M*N, the unit of the paper's throughput figures).
 e2e    = the same metric through the public API with host buffers: fr_set_state from pinned host
          arrays, the cycle, fr_get_leaves + fr_get_state back to host, every step.
 --impl reference times the CPU oracle (single thread) on the same workload, one cycle per step.
