@@ -384,20 +384,12 @@ def test_paper_uniform_l2_error(p, dt, tol):
     assert abs(l2 - expect) < tol * expect, (l2, expect)
 
 
-@pytest.mark.skipif(not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS (about 5 minutes)")
-def test_paper_large_domain_adaptive_row():
-    # The paper's adaptive table for the large domain (Sec. 5.2; 100 wide: its element counts,
-    # 65536 at dx = 25/64, fix the width the text misprints; one period t = 100): p = 1, Dmax 8
-    # prints L2 4.64e-2 and 961 elements.  Its initial mesh is read top-down: uniform at Dmax,
-    # then Dmax - Dmin passes of the criterion (coarsening), then the exact state at the leaves.
-    # (Bottom-up from Dmin, as the library builds its initial mesh, leaves this mesh uniform at
-    # Dmin: its 12.5-wide elements never hold more points inside radius 5 than beyond 6, and the
-    # error comes out 2.8x larger; on the small domain both readings give the same run.)
-    L, p, Dmax, n = 100.0, 1, 8, 2
-    cfg = paper_uniform_cfg(p, Dmax, 0.001)
-    cfg.update(L=L, Dbase=3, Dmax=Dmax, init_passes=0, indicator=1, th_refine=5.0, th_coarsen=6.0,
-               adapt_every=10, vort=np.array([[L / 2, L / 2, 5.0, 1.0]]))
-    m = O.OracleMesh(cfg)
+def paper_topdown_start(m, cfg):
+    """Top-down initial adaptive mesh for the paper's runs on a mesh object `m` with the oracle's
+    (or the CUDA binding's) calls: uniform at Dmax with the closed-form state, Dmax - Dbase
+    adaptations by the mesh's own criterion (which coarsen away from the vortex), then the
+    closed-form state at the leaves and t = 0.  2D."""
+    L, p, Dmax, n = cfg["L"], cfg["p"], cfg["Dmax"], cfg["p"] + 1
     x = O.operators(p)["x"]
 
     def exact_state(keys):
@@ -413,11 +405,27 @@ def test_paper_large_domain_adaptive_row():
     boxes = np.array([(Dmax, i, j, 0) for i in range(nc) for j in range(nc)], dtype=np.int32)
     keys = np.sort(O.morton_encode(2, Dmax, boxes))
     m.set_state(keys, exact_state(keys))
-    for _ in range(Dmax - 3):
+    for _ in range(Dmax - cfg["Dbase"]):
         m.adapt()
-    keys = m.leaves()
+    keys = np.ascontiguousarray(m.leaves())
     m.set_state(keys, exact_state(keys))
     m.set_time(0.0)
+
+
+@pytest.mark.skipif(not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS (about 5 minutes)")
+def test_paper_large_domain_adaptive_row():
+    # The paper's adaptive table for the large domain (Sec. 5.2; 100 wide: its element counts,
+    # 65536 at dx = 25/64, fix the width the text misprints; one period t = 100): p = 1, Dmax 8
+    # prints L2 4.64e-2 and 961 elements.  Its initial mesh is read top-down (paper_topdown_start).
+    # (Bottom-up from Dmin, as the library builds its initial mesh, leaves this mesh uniform at
+    # Dmin: its 12.5-wide elements never hold more points inside radius 5 than beyond 6, and the
+    # error comes out 2.8x larger; on the small domain both readings give the same run.)
+    L = 100.0
+    cfg = paper_uniform_cfg(1, 8, 0.001)
+    cfg.update(L=L, Dbase=3, init_passes=0, indicator=1, th_refine=5.0, th_coarsen=6.0,
+               adapt_every=10, vort=np.array([[L / 2, L / 2, 5.0, 1.0]]))
+    m = O.OracleMesh(cfg)
+    paper_topdown_start(m, cfg)
     for _ in range(10000):
         m.step(10)
         m.adapt()
