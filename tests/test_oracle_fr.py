@@ -412,16 +412,17 @@ def paper_topdown_start(m, cfg):
     m.set_time(0.0)
 
 
-@pytest.mark.skipif(not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS (about 5 minutes)")
-def test_paper_large_domain_adaptive_row():
+@pytest.mark.skipif(not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS (5, 10, 16 minutes)")
+@pytest.mark.parametrize("p,expect,count", [(1, 4.64e-2, 961), (2, 1.18e-3, 952), (3, 2.68e-5, 952)])
+def test_paper_large_domain_adaptive_row(p, expect, count):
     # The paper's adaptive table for the large domain (Sec. 5.2; 100 wide: its element counts,
-    # 65536 at dx = 25/64, fix the width the text misprints; one period t = 100): p = 1, Dmax 8
-    # prints L2 4.64e-2 and 961 elements.  Its initial mesh is read top-down (paper_topdown_start).
+    # 65536 at dx = 25/64, fix the width the text misprints; one period t = 100), Dmax 8 rows:
+    # printed L2 and element count.  Its initial mesh is read top-down (paper_topdown_start).
     # (Bottom-up from Dmin, as the library builds its initial mesh, leaves this mesh uniform at
     # Dmin: its 12.5-wide elements never hold more points inside radius 5 than beyond 6, and the
     # error comes out 2.8x larger; on the small domain both readings give the same run.)
     L = 100.0
-    cfg = paper_uniform_cfg(1, 8, 0.001)
+    cfg = paper_uniform_cfg(p, 8, 0.001)
     cfg.update(L=L, Dbase=3, init_passes=0, indicator=1, th_refine=5.0, th_coarsen=6.0,
                adapt_every=10, vort=np.array([[L / 2, L / 2, 5.0, 1.0]]))
     m = O.OracleMesh(cfg)
@@ -430,5 +431,5 @@ def test_paper_large_domain_adaptive_row():
         m.step(10)
         m.adapt()
     assert abs(m.info()["t"] - 100.0) < 1e-9
-    assert abs(m.norms()["l2_rho"] - 4.64e-2) < 0.02 * 4.64e-2
-    assert m.M == 961
+    assert abs(m.norms()["l2_rho"] - expect) < 0.02 * expect
+    assert m.M == count
