@@ -331,8 +331,11 @@ struct RkT<ff> {
 };
 
 // element stage: R = -sum_a (2/h) [ sum_j Dt_ij f_j + gL_i F(-1) + gR_i F(+1) ] along each axis
-// (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt), then
-// out = a*un + b*us + c*R (Eq. rk3), and (optionally) the traces of out.
+// (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt; the interface kernel
+// stores 2F and the slopes carry the 1/2), then out = a*un + b*us + c*R (Eq. rk3), and
+// (optionally) the traces of out.  Phases: stage state -> pointwise fluxes -> volume sums
+// sum_j Dt_ij f_j, all before the wait on the interface kernel; then its common fluxes ->
+// correction terms, Runge-Kutta combination, traces.
 template <int DIM, int NP, class T>
 __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
   using S = Sz<DIM, NP>;
