@@ -111,3 +111,30 @@ def face_neighbours(dim, Dmax, boxes, e, f):
 def child_bits(dim, Dmax, B):
     w = width(Dmax, B[0])
     return [(B[1 + a] // w) & 1 for a in range(dim)]
+
+
+def parent(Dmax, A):
+    w = width(Dmax, A[0] - 1)
+    return (A[0] - 1, A[1] // w * w, A[2] // w * w, A[3] // w * w)
+
+
+def edit(dim, Dmax, Dbase, boxes, flags):
+    """The refine/coarsen edit by its definition (Sec. 4.1), with refinement clamped at Dmax and
+    coarsening at Dbase: a leaf flagged 1 below Dmax becomes its 2^dim children; a complete group
+    of 2^dim sibling leaves, every one flagged -1 and deeper than Dbase, becomes its parent; every
+    other leaf stays.  Returns the edited leaves (sorted) and the parents that fused."""
+    boxes = [tuple(b) for b in boxes]
+    pos = {b: i for i, b in enumerate(boxes)}
+    out, fused = set(), set()
+    for i, b in enumerate(boxes):
+        if flags[i] == 1 and b[0] < Dmax:
+            out.update(children(dim, Dmax, b))
+            continue
+        if flags[i] == -1 and b[0] > Dbase:
+            par = parent(Dmax, b)
+            if all(k in pos and flags[pos[k]] == -1 for k in children(dim, Dmax, par)):
+                out.add(par)
+                fused.add(par)
+                continue
+        out.add(b)
+    return sorted(out), sorted(fused)

@@ -433,3 +433,66 @@ def test_paper_large_domain_adaptive_row(p, expect, count):
     assert abs(m.info()["t"] - 100.0) < 1e-9
     assert abs(m.norms()["l2_rho"] - expect) < 0.02 * expect
     assert m.M == count
+
+
+def _solution_points(dim, p, Dmax, L, keys):
+    """Physical coordinates [M][N][3] of each leaf's Gauss-Legendre solution points (nodes from
+    numpy's Gauss-Legendre rule, x fastest in the point index) and the leaf widths h."""
+    n, N = p + 1, (p + 1) ** dim
+    xi, _ = np.polynomial.legendre.leggauss(n)
+    bx = O.morton_decode(dim, Dmax, keys)
+    h = L / 2.0 ** bx[:, 0]
+    cell = L / 2.0 ** Dmax
+    idx = np.arange(N)
+    X = np.zeros((keys.shape[0], N, 3))
+    for a in range(dim):
+        ia = (idx // n ** a) % n
+        X[:, :, a] = bx[:, 1 + a, None] * cell + (xi[ia][None, :] + 1) / 2 * h[:, None]
+    return X, h
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax,seed", [(2, 1, 2, 5, 1), (2, 2, 2, 5, 2), (2, 3, 2, 5, 3),
+                                                   (2, 4, 2, 5, 4), (3, 1, 1, 3, 4), (3, 2, 1, 3, 5),
+                                                   (3, 3, 1, 3, 9)])
+def test_density_gradient_indicator(dim, p, Dbase, Dmax, seed):
+    # eta = h * max over the solution points of |grad rho| (the density-gradient reading of the
+    # indicator, Sec. 5.2), on a nonconforming tree:
+    # * rho linear along each axis and along an oblique direction b: the degree-p interpolant is
+    #   exact, so eta = h |b| in every element (a dropped 2/h, a missing square root or a wrong
+    #   axis fails);
+    # * for p >= 2, rho = c (x_a - x0)^2 + beta x_b: the gradient varies over the element, so eta
+    #   = h * max_i sqrt((2c (x_a,i - x0))^2 + beta^2) pins the set the maximum runs over;
+    # * flags: 1 above the refine threshold, -1 below the coarsen threshold, from the expected eta.
+    # Tolerance: eta is formed from O(1) densities by an n-term sum with |D_ij| <= n^2, so its
+    # rounding error is ~n^3 * 3 * 2^-53 absolute in reference coordinates against a gradient of
+    # h|b|/2 >= 0.05 there: 1e-12 relative.
+    cfg, _, keys = _random_nonconforming_mesh(dim, p, Dbase, Dmax, seed, 0.35)
+    M, nv, N = keys.shape[0], dim + 2, (p + 1) ** dim
+    X, h = _solution_points(dim, p, Dmax, cfg["L"], keys)
+    bnorm = 0.37
+    th_r, th_c = 0.99 * bnorm * h.max(), 1.01 * bnorm * h.min()
+    assert th_r > th_c
+    cfg = dict(cfg, indicator=0, th_refine=th_r, th_coarsen=th_c)
+    m = O.OracleMesh(cfg)
+    cases = []
+    for a in range(dim):
+        cases.append((2.0 + bnorm * X[:, :, a], h * bnorm))
+    b = np.array([0.21, -0.33, 0.12 if dim == 3 else 0.0])
+    cases.append((2.0 + X @ b, h * np.linalg.norm(b)))
+    if p >= 2:
+        x0, c, beta = 0.3 * cfg["L"], 0.05, 0.11
+        for a in range(dim):
+            o = (a + 1) % dim
+            g = np.sqrt((2 * c * (X[:, :, a] - x0)) ** 2 + beta ** 2)
+            cases.append((2.0 + c * (X[:, :, a] - x0) ** 2 + beta * X[:, :, o], h * g.max(axis=1)))
+    for k, (rho, want) in enumerate(cases):
+        u = np.zeros((M, nv, N))
+        u[:, 0] = rho
+        u[:, -1] = 1.0 / (cfg["gamma"] - 1.0)
+        m.set_state(keys, u)
+        flags, eta = m.flags()
+        assert np.max(np.abs(eta - want) / want) < 1e-12
+        expect = np.where(want > th_r, 1, np.where(want < th_c, -1, 0))
+        assert np.array_equal(flags, expect)
+        if k == 0:  # the thresholds sit just inside the coarsest and finest h: all three flags occur
+            assert set(expect.tolist()) == {-1, 0, 1} or len(set(h.tolist())) == 2

@@ -269,3 +269,30 @@ def test_vectorised_draws_match_splitmix64():
         assert np.array_equal(W.random_uniform(257, seed), want)
     p = W.torus_points(1000, 3)
     assert p.shape == (1000, 3) and p.min() > 0.0 and p.max() < 1.0
+
+
+@pytest.mark.parametrize("dim,Dbase,Dmax,seed,ps", [(2, 2, 5, 31, 0.25), (2, 2, 6, 33, 0.25), (2, 1, 5, 41, 0.3),
+                                                    (3, 1, 3, 42, 0.25), (3, 1, 4, 43, 0.12)])
+def test_adapt_keys_is_balance_of_brute_edit(dim, Dbase, Dmax, seed, ps):
+    # Sec. 4.1 (edit, then 2:1 balance): the oracle's adaptation equals the brute-force edit by its
+    # definition (refine flagged leaves, fuse complete all -1 sibling groups above Dbase) followed
+    # by the brute-force balance closure; some fused parents must survive the balance, so an edit
+    # that ignored the coarsening flags would fail here
+    boxes, keys = _tree(dim, Dbase, Dmax, seed, ps)
+    keys = O.balance(dim, Dmax, keys)
+    M = keys.shape[0]
+    ob = [tuple(b) for b in O.morton_decode(dim, Dmax, keys)]
+    flags = W.random_flags(M, seed + 100, p_refine=0.1, p_coarsen=0.4)
+    coin = W.random_uniform(M, seed + 200)
+    pos = {b: i for i, b in enumerate(ob)}
+    for i, b in enumerate(ob):
+        if b[0] <= Dbase or coin[i] > 0.6:
+            continue
+        kids = brute.children(dim, Dmax, brute.parent(Dmax, b))
+        if kids[0] == b and all(k in pos for k in kids):
+            for k in kids:
+                flags[pos[k]] = -1
+    new = [tuple(b) for b in O.morton_decode(dim, Dmax, O.adapt_keys(dim, Dbase, Dmax, keys, flags))]
+    edited, fused = brute.edit(dim, Dmax, Dbase, ob, flags)
+    assert sorted(new) == brute.balance(dim, Dmax, edited)
+    assert any(f in set(new) for f in fused), "no fused parent survived: the case pins nothing"
