@@ -239,7 +239,8 @@ int fr_keys_sort(int dim, int Dmax, uint64_t* d_keys, int64_t n, void* stream);
    every GPU that loads the library until the process exits), so n is limited to
    FR_NOALLOC_SORT_MAX_KEYS; larger n returns FR_EINVAL without touching the keys.
    The first call on each device looks up that array's device address (cudaGetSymbolAddress);
-   make that first call before any stream capture.  All calls share the one array and every call
+   make that first call before any stream capture.  That lookup is safe when several host threads
+   make their first calls on a device at the same time.  All calls share the one array and every call
    writes the scratch words it later reads, so no clearing is needed between calls, but calls
    whose GPU work overlaps (for example on two streams at once) race on the scratch and must be
    serialised by the caller.  Synchronises `stream` before returning. */

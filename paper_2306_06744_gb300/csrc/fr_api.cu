@@ -30,6 +30,7 @@ struct fr_mesh {
   Buf<int32_t> nbr, conf, hang, contrib;
   Buf<int8_t> ftype, slot, flags;
   int64_t n_conf = 0, n_hang = 0;
+  bool traces_ok = false;  // trace holds the traces of the current state u
   Buf<double> norm_part, norm_out;
   Buf<unsigned long long> dmax;
   Buf<float> mlp_params;  // learned indicator weights (FP32 master copy), empty if none
@@ -168,13 +169,18 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   return 0;
 }
 
-// after the synchronisation: checks the flags (bad[0] 2:1 violation, bad[1] mapping), keeps the
-// face-list counts and the per-hanging-face contributor table
-static int conn_finish(fr_mesh* m, int64_t faces, const int32_t* hb, Buf<int32_t>& hcon) {
-  Err* err = &m->err;
-  if (hb[0]) return set_error(err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
+// after the synchronisation: the flags of conn_issue and the mapping (bad[0] 2:1 violation,
+// bad[1] a new leaf the mapping could not place)
+static int conn_check(fr_mesh* m, const int32_t* hb) {
+  if (hb[0]) return set_error(&m->err, FR_EINVAL, "tree is not 2:1 balanced (connectivity)");
   if (hb[1])
-    return set_error(err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
+    return set_error(&m->err, FR_EINVAL, "mapping found a new leaf that is neither kept, refined nor fused");
+  return 0;
+}
+
+// after conn_check: keeps the face-list counts and the per-hanging-face contributor table
+static int conn_finish(fr_mesh* m, int64_t faces, const int32_t* hb, Buf<int32_t>& hcon) {
+  FR_TRY(conn_check(m, hb));
   m->n_conf = faces & 0xFFFFFFFFll;
   m->n_hang = faces >> 32;
   Buf<int32_t> old = m->contrib;  // the per element-face table is not needed after the lists
@@ -216,7 +222,29 @@ int ensure_state(fr_mesh* m, int64_t M) {
 }
 
 int refresh_traces(fr_mesh* m) {
-  return launch_traces(m->cfg.precision, m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err);
+  m->traces_ok = false;
+  FR_TRY(launch_traces(m->cfg.precision, m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err));
+  m->traces_ok = true;
+  return 0;
+}
+
+// The time-step buffers of the current tree.  An allocation that fails late in an adaptation or a
+// state upload can leave them missing or short (Buf::ensure releases a block before it allocates
+// the larger one); they are grown again here, and the traces recomputed, before anything reads
+// them, so a failed call leaves the mesh usable.
+int ready_buffers(fr_mesh* m) {
+  const size_t M = size_t(m->M);
+  if (!m->u.p || m->u.cap < M * m->EU || !m->keys.p || m->keys.cap < M)
+    return set_error(&m->err, FR_EINVAL, "the mesh lost its state in an earlier failed call");
+  FR_TRY(m->w.ensure(m->A, M * m->EU));
+  FR_TRY(m->fcomm.ensure(m->A, M * m->EF));
+  FR_TRY(m->flags.ensure(m->A, M));
+  if (!m->trace.p || m->trace.cap < M * m->EF) {
+    m->traces_ok = false;
+    FR_TRY(m->trace.ensure(m->A, M * m->EF));
+  }
+  if (!m->traces_ok) FR_TRY(refresh_traces(m));
+  return 0;
 }
 
 FaceArgs face_args(fr_mesh* m) {
@@ -358,6 +386,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<double> nu;
   Buf<int32_t> src, hcon;
   Buf<int8_t> tag;
+  bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
   int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
@@ -374,13 +403,20 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       T.mark(1);
     }
     T.mark(2);
-    if (!r) r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon);
+    if (!r) {
+      conn_dirty = true;
+      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon);
+    }
     if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaMemcpyAsync(&hs, m->status.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaStreamSynchronize(s) != cudaSuccess))
       r = set_error(err, FR_ECUDA, "adapt read");
-    if (!r && hs) r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator)");
+    if (!r && hs) {
+      r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator)");
+      // reported once: the status word starts clear for the next call
+      if (cudaMemsetAsync(m->status.p, 0, 4, s) != cudaSuccess) cudaGetLastError();
+    }
     return r;
   };
   if (!rc && fast) {
@@ -400,13 +436,31 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     rc = tree_balance(m->dim, m->g, m->g.Dmax, Dlow, nk, ctl, n_ub, h_ctl, m->A, s, err);
   }
   if (!rc && !fast) rc = rest(h_ctl[CTL_N], nullptr);
+  if (!rc) rc = conn_check(m, hb);
   const int64_t M1 = h_ctl[CTL_N];
   src.release(m->A);
   tag.release(m->A);
+  if (!rc) {
+    // the time-step buffers for the new size, while the mesh still holds the old tree (a block
+    // that is released and not replaced here is grown again by ready_buffers)
+    m->traces_ok = false;
+    rc = m->w.ensure(m->A, size_t(M1) * m->EU);
+    if (!rc) rc = m->trace.ensure(m->A, size_t(M1) * m->EF);
+    if (!rc) rc = m->fcomm.ensure(m->A, size_t(M1) * m->EF);
+    if (!rc) rc = m->flags.ensure(m->A, size_t(M1));
+    if (!rc && !transfer) rc = m->u.ensure(m->A, size_t(M1) * m->EU);
+  }
   if (rc) {
+    // nothing of the mesh changed but the connectivity tables: rebuild them for the current tree
+    // (keeping this call's error), so the mesh stays usable
     nk.release(m->A);
     nu.release(m->A);
     hcon.release(m->A);
+    if (conn_dirty) {
+      Err keep = *err;
+      rebuild_conn(m);
+      *err = keep;
+    }
     return rc;
   }
   Buf<uint64_t> ok = m->keys;
@@ -418,14 +472,10 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     m->u = nu;
     ou.release(m->A);
   }
+  m->traces_ok = false;
   rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
   hcon.release(m->A);
   FR_TRY(rc);
-  FR_TRY(m->w.ensure(m->A, size_t(M1) * m->EU));
-  FR_TRY(m->trace.ensure(m->A, size_t(M1) * m->EF));
-  FR_TRY(m->fcomm.ensure(m->A, size_t(M1) * m->EF));
-  FR_TRY(m->flags.ensure(m->A, size_t(M1)));
-  if (!transfer) FR_TRY(m->u.ensure(m->A, size_t(M1) * m->EU));
   if (transfer) FR_TRY(refresh_traces(m));
   T.mark(3);
   if (st) {
@@ -594,6 +644,7 @@ void fr_mesh_free(fr_mesh* m) {
 
 int fr_step(fr_mesh* m, int nsteps, fr_step_stats* st) {
   if (!m || nsteps < 0) return set_error(m ? &m->err : global_err(), FR_EINVAL, "bad arguments");
+  FR_TRY(ready_buffers(m));
   Timer T(st != nullptr, m->stream);
   T.mark(0);
   for (int k = 0; k < nsteps; ++k) FR_TRY(rk3_step(m));
@@ -636,12 +687,14 @@ int fr_run(fr_mesh* m, int nsteps, fr_step_stats* sst, fr_adapt_stats* ast) {
 
 int fr_adapt(fr_mesh* m, const int8_t* dev_flags, fr_adapt_stats* st) {
   if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
+  FR_TRY(ready_buffers(m));
   return adapt_impl(m, dev_flags, st, true);
 }
 
 int fr_flags(fr_mesh* m, int8_t* host_flags, double* host_eta, int64_t cap) {
   if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
   if (cap < m->M) return set_error(&m->err, FR_EOVERFLOW, "capacity below M");
+  FR_TRY(ready_buffers(m));
   Buf<double> eta;
   if (host_eta) FR_TRY(eta.ensure(m->A, m->M));
   if (m->cfg.indicator == 2) {
@@ -661,6 +714,7 @@ int fr_rhs(fr_mesh* m, double* host_R, int64_t cap) {
   if (!m) return set_error(global_err(), FR_EINVAL, "null mesh");
   int64_t S = m->M * m->EU;
   if (cap < S) return set_error(&m->err, FR_EOVERFLOW, "capacity below M*nv*N");
+  FR_TRY(ready_buffers(m));
   FR_TRY(stage(m, m->u.p, nullptr, m->w.p, 0.0, 0.0, 1.0, false));
   return host_copy(&m->err, host_R, m->w.p, size_t(S) * 8, cudaMemcpyDeviceToHost, m->stream);
 }
@@ -744,6 +798,7 @@ int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double*
   Buf<double> ou = m->u;  // the stage buffer holding the new state becomes the state
   m->u = m->w;
   m->w = ou;
+  m->traces_ok = false;
   rc = conn_finish(m, h, hb, hcon);
   hcon.release(m->A);
   FR_TRY(rc);

@@ -1,5 +1,6 @@
 // fr_prim.cu -- device-wide primitives without CUB: exclusive scan (reduce-then-scan, no
 // inter-block waits), stable LSD radix sort of uint64 keys (warp-match ranking), device memory.
+#include <atomic>
 #include <cstdio>
 
 #include "fr_internal.cuh"
@@ -397,22 +398,26 @@ constexpr size_t NA_BYTES = NA_OFF_TOT + 256;
 static __device__ __align__(256) unsigned char g_noalloc_sort_scratch[NA_BYTES];
 
 constexpr int NA_MAX_DEVICES = 64;
-unsigned char* g_noalloc_ptr[NA_MAX_DEVICES] = {nullptr};
+// per device, the looked-up address; atomic, because host threads may make their first calls on
+// a device at the same time (each looks the address up and stores the same value)
+std::atomic<unsigned char*> g_noalloc_ptr[NA_MAX_DEVICES];
 
 // device address of the scratch array on the current device (looked up on first use)
 int noalloc_scratch(unsigned char** out, Err* err) {
   int dev = 0;
   FR_CUDA(err, cudaGetDevice(&dev));
   if (dev < 0 || dev >= NA_MAX_DEVICES) return set_error(err, FR_EINVAL, "device index too large");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t ce = cudaGetSymbolAddress(&p, g_noalloc_sort_scratch);
-    if (ce != cudaSuccess || !p)
+  unsigned char* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void* q = nullptr;
+    cudaError_t ce = cudaGetSymbolAddress(&q, g_noalloc_sort_scratch);
+    if (ce != cudaSuccess || !q)
       return set_error(err, FR_ECUDA, std::string("cudaGetSymbolAddress(sort scratch): ") +
                                           cudaGetErrorString(ce));
-    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    p = static_cast<unsigned char*>(q);
+    g_noalloc_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_noalloc_ptr[dev];
+  *out = p;
   return 0;
 }
 

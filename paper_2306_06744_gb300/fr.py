@@ -184,13 +184,23 @@ def make_config(cfg: dict):
 
 
 class _TorchAllocator:
-    """Hands torch's CUDA caching allocator to the library."""
+    """Hands torch's CUDA caching allocator to the library.
+
+    ``fail_in``: host-side failure injection for tests of the library's error paths: when set to
+    k >= 0, the allocation after the next k returns NULL (the library then reports FR_ENOMEM),
+    and the counter clears itself.  No GPU fault is involved."""
 
     def __init__(self, device):
         torch = _torch()
         self.device = device
+        self.fail_in = None
 
         def _alloc(nbytes, stream, ctx):
+            if self.fail_in is not None:
+                if self.fail_in == 0:
+                    self.fail_in = None
+                    return None
+                self.fail_in -= 1
             try:
                 return torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0))
             except Exception:  # the library reports FR_ENOMEM on NULL

@@ -37,6 +37,38 @@ def test_noalloc_sort_matches_allocating_sort_twice():
         assert np.array_equal(got, ref), call
 
 
+def test_noalloc_sort_small_sizes_and_no_allocation():
+    # n <= 1 returns at once; up to 16384 keys the digit histogram fits one scan tile (the
+    # one-level scan branch); the larger sizes above take the two-level scan
+    import torch
+    lib = fr.load()
+    rng = np.random.default_rng(7)
+    for n in (0, 1, 2, 1000, 16384):
+        keys = rng.integers(0, 1 << 40, size=n, dtype=np.uint64)
+        if n >= 4:
+            keys[: n // 4] = keys[n // 4: n // 2]
+        if n == 0:
+            b = torch.zeros(0, dtype=torch.int64, device="cuda")
+            stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            assert lib.fr_keys_sort_noalloc(3, 10, ctypes.c_void_p(b.data_ptr()), 0, stream) == 0
+            continue
+        ref, got = _sort_both(lib, torch, keys, 3, 10)
+        assert np.array_equal(ref, np.sort(keys)), n
+        assert np.array_equal(got, ref), n
+    # the call allocates nothing: the device's free memory is the same before and after calls
+    # (the first call on the device, which may load the library's module, was made above)
+    keys = rng.integers(0, 1 << 40, size=50000, dtype=np.uint64)
+    b = torch.from_numpy(keys.view(np.int64)).cuda()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert lib.fr_keys_sort_noalloc(3, 10, ctypes.c_void_p(b.data_ptr()), b.numel(), stream) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(b.cpu().numpy().view(np.uint64), np.sort(keys))
+
+
 def test_noalloc_sort_rejects_oversize():
     import torch
     lib = fr.load()
