@@ -531,7 +531,10 @@ def main():
     # the FP64 mesh is not needed any more: its ~67 GB (largest workload) go back to the cache
     mesh.close()
     if not args.no_forms:
-        for prec, name in ((1, "f32_mixed_f64_rk"), (2, "f64x2f32_double_word")):
+        forms_run = [(1, "f32_mixed_f64_rk"), (4, "f64x2f32_double_word")]
+        if (dim, p) == (3, 3):  # the tensor-core operator forms are built for 3D p = 3
+            forms_run[1:1] = [(2, "tf32_tensor_core_f64_rk"), (3, "bf16x3_tensor_core_f64_rk")]
+        for prec, name in forms_run:
             fm = fr.Mesh(dict(cfg, precision=prec), stream=stream)
             for _ in range(args.warmup):
                 fm.step(ae)

@@ -76,8 +76,15 @@ typedef struct {
   double th_refine, th_coarsen;
   int32_t precision;       /* arithmetic of the time-step kernels (state, norms and adaptation are
                               always FP64): 0 FP64; 1 FP32 fluxes, operators, traces and common
-                              fluxes with the Runge-Kutta combination in FP64; 2 double-word
-                              (two-float, ~48-bit significand) on the FP32 pipes                    */
+                              fluxes with the Runge-Kutta combination in FP64; 2 as 1 with the
+                              element's flux-derivative contraction on the tensor cores in TF32
+                              (FP32 accumulation); 3 the same in split BF16 (bf16x3: hi*hi +
+                              hi*lo + lo*hi, FP32 accumulation); 4 double-word (two-float, ~48-bit
+                              significand) on the FP32 pipes.  2 and 3 are built for dim 3, p 3
+                              (64-point hexahedra, Sec. 2.1's operator as 16 x 16 Kronecker blocks);
+                              other dim/p return FR_EINVAL.  A tensor-core completion wait that
+                              gives up is reported as FR_ETIMEOUT by the next fr_adapt/fr_run
+                              adaptation                                                          */
   int32_t init_passes;     /* < 0: Dmax-Dbase passes of {closed-form state, flags, adaptation}    */
 } fr_config;
 
@@ -187,6 +194,13 @@ const char* fr_last_error(const fr_mesh* m);
    indicator).  fr_mlp_grad and fr_mlp_train_step run on the tensor cores too (batch tiles of 128
    samples, weight gradients accumulated in tensor memory, block partials summed in a fixed order:
    deterministic), with the same FR_ETIMEOUT behaviour. */
+/* Bound, in SM clock cycles, of the tensor-core inference kernel's waits on its own copies and MMAs
+   (fr_mlp_forward and the learned indicator); cycles <= 0 restores the default of about a second.
+   A wait that reaches the bound makes the call return FR_ETIMEOUT; each block then drains what it
+   issued (with the default bound), frees its tensor memory and exits, so the device stays usable.
+   A bound shorter than an MMA's latency forces that path (used by the tests).  Process-wide,
+   not thread-safe. */
+void fr_tc_set_wait_limit(long long cycles);
 int fr_mlp_param_count(int in_dim);
 int fr_features(fr_mesh* m, void* d_X_bf16, int64_t cap, int32_t* in_dim);
 int fr_set_learned_indicator(fr_mesh* m, const float* host_params, int64_t n);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfr_gb300.so")
 SOURCES = ["fr_prim.cu", "fr_tree.cu", "fr_solver.cu", "fr_api.cu", "fr_prec_f64.cu",
-           "fr_prec_f32.cu", "fr_prec_ff.cu", "fr_mlp.cu"]
+           "fr_prec_f32.cu", "fr_prec_ff.cu", "fr_mlp.cu", "fr_tc_stage.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC,
          "--expt-relaxed-constexpr"]

@@ -31,6 +31,7 @@ struct fr_mesh {
   Buf<int8_t> ftype, slot, flags;
   int64_t n_conf = 0, n_hang = 0;
   bool traces_ok = false;  // trace holds the traces of the current state u
+  bool flags_fresh = false;  // flags hold the density-gradient flags of u (from the last stage)
   Buf<double> norm_part, norm_out;
   Buf<unsigned long long> dmax;
   Buf<float> mlp_params;  // learned indicator weights (FP32 master copy), empty if none
@@ -63,28 +64,6 @@ namespace {
 
 constexpr int TB = 256;
 inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); }
-
-// faces per element: conforming faces owned by their minus side (checked on the plus face of
-// each element), coarse sides of hanging faces
-template <int DIM>
-__global__ void k_face_count(const int8_t* __restrict__ ftype, int64_t M_ub, const int64_t* __restrict__ d_M,
-                             int64_t* __restrict__ c) {
-  pdl_wait_then_release();
-  int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= M_ub) return;
-  if (d_M && e >= *d_M) {
-    c[e] = 0;
-    return;
-  }
-  int a = 0, b = 0;
-#pragma unroll
-  for (int f = 0; f < 2 * DIM; ++f) {
-    int8_t t = ftype[e * 2 * DIM + f];
-    a += (f & 1) && t == 0;
-    b += t == 2;
-  }
-  c[e] = int64_t(a) | (int64_t(b) << 32);  // conforming count low, hanging count high
-}
 
 template <int DIM>
 __global__ void k_face_write(const int8_t* __restrict__ ftype, const int32_t* __restrict__ contrib,
@@ -125,7 +104,9 @@ int check_cfg(const fr_config* c, Err* err) {
   if (c->nvort < 0 || c->nvort > 16 || (c->nvort > 0 && !c->vort))
     return set_error(err, FR_EINVAL, "nvort must be in 0..16 with a vortex array");
   if (c->indicator < 0 || c->indicator > 3) return set_error(err, FR_EINVAL, "bad indicator");
-  if (c->precision < 0 || c->precision > 2) return set_error(err, FR_EINVAL, "precision must be 0, 1 or 2");
+  if (c->precision < 0 || c->precision > 4) return set_error(err, FR_EINVAL, "precision must be 0..4");
+  if ((c->precision == 2 || c->precision == 3) && !(c->dim == 3 && c->p == 3))
+    return set_error(err, FR_EINVAL, "the tensor-core operator forms (precision 2, 3) are built for 3D p = 3");
   if (!(c->dt > 0) && !(c->cfl > 0)) return set_error(err, FR_EINVAL, "need dt > 0 or cfl > 0");
   return 0;
 }
@@ -146,12 +127,8 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   int64_t* cnt = Sc.get<int64_t>(n_ub);
   int64_t* off = Sc.get<int64_t>(n_ub);
   if (!cnt || !off) return set_error(err, FR_ENOMEM, "conn scratch");
-  FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err));
-  if (m->dim == 2)
-    launch_dependent(k_face_count<2>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
-  else
-    launch_dependent(k_face_count<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p), n_ub, d_n, cnt);
-  FR_LAUNCH_CHECK(err);
+  // connectivity and the per-leaf face-list counts in one kernel
+  FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err, cnt));
   Offs O;
   FR_TRY(scan_counts64_local(cnt, off, n_ub, d_faces, Sc, s, err, &O));
   // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
@@ -262,7 +239,7 @@ FaceArgs face_args(fr_mesh* m) {
 }
 
 int stage(fr_mesh* m, const double* us, const double* un, double* out, double a, double b, double c,
-          bool traces) {
+          bool traces, int8_t* flags = nullptr) {
   cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
   const bool rec = m->prof && (m->prof_count++ % m->prof_stride) == 0;
   if (rec) {
@@ -291,6 +268,10 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.a = a;
   S.b = b;
   S.c = c;
+  S.status = m->status.p;
+  S.flags = flags;
+  S.th_r = m->cfg.th_refine;
+  S.th_c = m->cfg.th_coarsen;
   FR_TRY(launch_stage(m->cfg.precision, m->dim, m->p, S, m->ops, m->stream, &m->err));
   if (rec) {
     cudaEventRecord(e2, m->stream);
@@ -301,11 +282,18 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
 
 // one SSP-RK3 step (Eq. rk3): u1 = u + dt R(u); u2 = 3/4 u + 1/4 u1 + 1/4 dt R(u1);
 // u^{n+1} = 1/3 u + 2/3 u2 + 2/3 dt R(u2).  Buffers: u holds u^n, w holds u1 then u2.
+// In the FP64 form with the density-gradient indicator, a step that ends on a multiple of
+// adapt_every also writes the flags of the new state from its last element kernel (the indicator
+// kernel of the next adaptation is then skipped).
 int rk3_step(fr_mesh* m) {
   double dt = m->dt;
+  m->flags_fresh = false;
+  const bool want = m->cfg.precision == 0 && m->cfg.indicator == 0 && m->cfg.adapt_every > 0 &&
+                    (m->step + 1) % m->cfg.adapt_every == 0;
   FR_TRY(stage(m, m->u.p, nullptr, m->w.p, 0.0, 1.0, dt, true));
   FR_TRY(stage(m, m->w.p, m->u.p, m->w.p, 0.75, 0.25, 0.25 * dt, true));
-  FR_TRY(stage(m, m->w.p, m->u.p, m->u.p, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true));
+  FR_TRY(stage(m, m->w.p, m->u.p, m->u.p, 1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0 * dt, true, want ? m->flags.p : nullptr));
+  m->flags_fresh = want;
   m->t += dt;
   m->step += 1;
   return 0;
@@ -326,6 +314,8 @@ int compute_flags(fr_mesh* m, double* eta) {
                         m->ops, X, m->stream, &m->err));
     return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->status.p, m->stream, &m->err);
   }
+  // flags the last time step already wrote for the current state
+  if (m->cfg.indicator == 0 && !eta && m->flags_fresh) return 0;
   // density gradient (indicator 0, and the fallback of the learned indicator) or analytic centre
   return launch_indicator(m->dim, m->p, m->cfg.indicator == 1 ? 1 : 0, m->cfg.th_refine, m->cfg.th_coarsen,
                           m->t, m->keys.p, m->M, m->g, m->prob, m->ops, m->u.p, m->flags.p, eta,
@@ -384,21 +374,19 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   int32_t hb[2] = {0, 0}, hs = 0;
   Buf<uint64_t> nk;
   Buf<double> nu;
-  Buf<int32_t> src, hcon;
-  Buf<int8_t> tag;
+  Buf<int32_t> hcon;
   bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
   int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
     int r = 0;
     if (transfer) {
-      if (!r) r = src.ensure(m->A, nb);
-      if (!r) r = tag.ensure(m->A, nb);
-      if (!r) r = tree_map(m->dim, m->g, m->keys.p, M0, nk.p, nb, d_n, src.p, tag.p, bad + 1, s, err);
+      // the mapping (Sec. 4.2) runs inside the transfer kernel, block by block
       T.mark(1);
       if (!r) r = nu.ensure(m->A, size_t(nb) * m->EU);
       if (!r)
-        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, nk.p, src.p, tag.p, nb, d_n, m->ops, m->u.p, nu.p, s, err);
+        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, nullptr, nullptr, bad + 1, nb, d_n, m->ops,
+                            m->u.p, nu.p, s, err);
     } else {
       T.mark(1);
     }
@@ -413,7 +401,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
                cudaStreamSynchronize(s) != cudaSuccess))
       r = set_error(err, FR_ECUDA, "adapt read");
     if (!r && hs) {
-      r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator)");
+      r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator or element kernel)");
       // reported once: the status word starts clear for the next call
       if (cudaMemsetAsync(m->status.p, 0, 4, s) != cudaSuccess) cudaGetLastError();
     }
@@ -438,8 +426,6 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   if (!rc && !fast) rc = rest(h_ctl[CTL_N], nullptr);
   if (!rc) rc = conn_check(m, hb);
   const int64_t M1 = h_ctl[CTL_N];
-  src.release(m->A);
-  tag.release(m->A);
   if (!rc) {
     // the time-step buffers for the new size, while the mesh still holds the old tree (a block
     // that is released and not replaced here is grown again by ready_buffers)
@@ -473,6 +459,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     ou.release(m->A);
   }
   m->traces_ok = false;
+  m->flags_fresh = false;
   rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
   hcon.release(m->A);
   FR_TRY(rc);
@@ -492,6 +479,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
 }
 
 int set_exact(fr_mesh* m, double t) {
+  m->flags_fresh = false;
   FR_TRY(launch_exact(m->dim, m->p, m->keys.p, m->M, m->g, t, m->prob, m->ops, m->u.p, m->stream, &m->err));
   m->t = t;
   return 0;
@@ -799,6 +787,7 @@ int fr_set_state(fr_mesh* m, const uint64_t* host_keys, int64_t M, const double*
   m->u = m->w;
   m->w = ou;
   m->traces_ok = false;
+  m->flags_fresh = false;
   rc = conn_finish(m, h, hb, hcon);
   hcon.release(m->A);
   FR_TRY(rc);
@@ -926,6 +915,8 @@ int fr_mlp_forward(int in_dim, const float* d_params, const void* d_X, int64_t n
   if (hs) return set_error(global_err(), FR_ETIMEOUT, "a tensor-core completion wait gave up");
   return 0;
 }
+
+void fr_tc_set_wait_limit(long long cycles) { mlp_set_wait_cycles(cycles); }
 
 int fr_mlp_grad(int in_dim, const float* d_params, const void* d_X, const int8_t* d_y, int64_t B,
                 const float* class_w, float* d_grad, float* d_loss, void* stream) {

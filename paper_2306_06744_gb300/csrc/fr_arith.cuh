@@ -1,9 +1,10 @@
 // fr_arith.cuh -- arithmetic types of the FR kernels.
 //
 //   double : native FP64 (precision 0).
-//   float  : FP32 operators, fluxes, traces and common fluxes (precision 1); the Runge-Kutta
-//            combination stays FP64.
-//   ff     : an unevaluated sum hi + lo of two floats ("double-word" arithmetic, precision 2),
+//   float  : FP32 operators, fluxes, traces and common fluxes (precision 1, and the tensor-core
+//            forms 2 and 3 outside their operator contraction); the Runge-Kutta combination
+//            stays FP64.
+//   ff     : an unevaluated sum hi + lo of two floats ("double-word" arithmetic, precision 4),
 //            ~48-bit significand on the FP32 pipes.  GB300 runs FP64 at 1/58 of its FP32 rate, so
 //            double-word arithmetic executes FP64-class accuracy several times faster.
 //
@@ -123,10 +124,25 @@ struct Ar<double> {
   static __device__ __forceinline__ double to_d(double x) { return x; }
   static __device__ __forceinline__ double c(double x) { return x; }
 };
+// double -> float by integer manipulation of the bit pattern (no FP64-rate conversion): the
+// significand is cut to 24 bits and rounded half away from zero (a carry moves into the exponent);
+// magnitudes below 2^-126 become a signed zero, above the float range infinity, NaN stays NaN.
+__device__ __forceinline__ float f32_from_double_bits(double x) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const uint32_t sign = uint32_t(b >> 63) << 31;
+  const int E = int((b >> 52) & 0x7FF) - 1023;
+  if (E < -126) return __int_as_float(int(sign));
+  if (E > 127)
+    return __int_as_float(int(sign | ((E == 1024 && (b & 0xFFFFFFFFFFFFFull)) ? 0x7FC00000u : 0x7F800000u)));
+  uint32_t mag = (uint32_t(E + 127) << 23) | uint32_t((b >> 29) & 0x7FFFFFu);
+  mag += uint32_t((b >> 28) & 1u);
+  return __int_as_float(int(sign | mag));
+}
+
 template <>
 struct Ar<float> {
-  static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
-  static __device__ __forceinline__ double to_d(float x) { return double(x); }
+  static __device__ __forceinline__ float from_d(double x) { return f32_from_double_bits(x); }
+  static __device__ __forceinline__ double to_d(float x) { return f_to_double_bits(x); }
 };
 template <>
 struct Ar<ff> {

@@ -247,6 +247,34 @@ __device__ __forceinline__ int64_t upper_bound_dev(const uint64_t* a, int64_t n,
   return lo;
 }
 
+// Old->new mapping of one new leaf (Sec. 4.2, mapping algorithm) by one lower bound in the old
+// keys: tag 0 copy of old leaf *src, 1 refined from old leaf *src, 2 fused from the 2^dim old
+// leaves starting at *src.  A new leaf that is none of these makes the tree pair invalid: *bad is
+// set and an in-bounds copy is emitted so later kernels stay in bounds.
+template <int DIM>
+__device__ __forceinline__ void map_leaf(const uint64_t* __restrict__ old, int64_t no, uint64_t key, const KG& g,
+                                         int32_t* src, int8_t* tag, int32_t* bad) {
+  const int64_t B = lower_bound_dev(old, no, key);
+  if (B < no && old[B] == key) {
+    *src = int32_t(B);
+    *tag = 0;
+  } else if (B > 0 && is_ancestor<DIM>(g, old[B - 1], key)) {
+    *src = int32_t(B - 1);
+    *tag = 1;
+  } else {
+    bool ok = B + (1 << DIM) <= no;
+    for (int c = 0; c < (1 << DIM) && ok; ++c) ok = old[B + c] == child_key<DIM>(g, key, c);
+    if (ok) {
+      *src = int32_t(B);
+      *tag = 2;
+    } else {
+      atomicExch(bad, 1);
+      *src = int32_t(B < no ? B : no - 1);
+      *tag = 0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Device memory: caller allocator or stream-ordered cudaMallocAsync.
 // ---------------------------------------------------------------------------------------------
@@ -387,11 +415,16 @@ int tree_complete(int dim, const KG& g, int Dmin, double L, const double* d_pts,
                   Buf<uint64_t>& out, int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
 int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf<uint64_t>& out,
                    int64_t* n_out, Alloc& A, cudaStream_t s, Err* err);
-// Control block of an adaptation on the device, CTL_SIZE int64 values (layout in fr_tree.cu):
+// Control block of an adaptation on the device, CTL_SLOTS int64 values (layout in fr_tree.cu):
 // [0] leaf count of the tree being built, [1] generated octants of the current balance pass,
 // [2] refined leaves, [3] coarsened groups, [4] overflowed pass depth (0: none), [5] passes that
-// changed the tree, [6] face-list counts (conforming | hanging << 32).
-enum { CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6, CTL_SLOTS = 8 };
+// changed the tree, [6] face-list counts (conforming | hanging << 32); for the merge of a balance
+// pass issued without synchronisation: [7] the leaf count before the pass, [8] the sorted
+// octants it merges.
+enum {
+  CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6,
+  CTL_NPREV = 7, CTL_GS = 8, CTL_SLOTS = 10
+};
 // The edit zeroes the control block (and the two error flags d_bad, if given) and leaves its
 // leaf count and statistics there without a host synchronisation; its output holds at most
 // n << dim leaves.
@@ -414,9 +447,12 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
              int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,
              cudaStream_t s, Err* err);
 // connectivity; d_contrib (may be null) receives [n][2dim][4] coarse-side contributors
+// d_fcnt (nullable): per leaf (n entries) the face-list counts, conforming faces owned (the + faces
+// of conforming pairs) in the low 32 bits and coarse sides of hanging faces in the high 32 bits;
+// zero past the device count
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
-              Err* err);
+              Err* err, int64_t* d_fcnt = nullptr);
 // sets *d_bad (not cleared here) unless keys are a complete sorted linear tree with depths in [Dlo, Dhi]
 int tree_validate_async(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
                         int32_t* d_bad, cudaStream_t s, Err* err);

@@ -17,6 +17,7 @@ namespace frg {
 template <class T>
 struct OpsT {
   T Dt[NPMAX][NPMAX];
+  T D[NPMAX][NPMAX];  // plain derivative l_j'(x_i) (density-gradient indicator)
   // gLh, gRh: half the correction slopes g'_L, g'_R at the solution points, because the
   // interface kernel stores twice the common flux (exact scalings by 2 and 1/2)
   T gLh[NPMAX], gRh[NPMAX], lm[NPMAX], lp[NPMAX];
@@ -43,6 +44,7 @@ OpsT<T> make_ops_t(const DevOps& o) {
     r.lp[i] = host_conv(o.lp[i], tag);
     for (int j = 0; j < NPMAX; ++j) {
       r.Dt[i][j] = host_conv(o.Dt[i][j], tag);
+      r.D[i][j] = host_conv(o.D[i][j], tag);
       for (int h = 0; h < 2; ++h) {
         r.I[h][i][j] = host_conv(o.I[h][i][j], tag);
         r.P[h][i][j] = host_conv(o.P[h][i][j], tag);
@@ -346,6 +348,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   __shared__ T sfl[EPB * DIM * EU];
   __shared__ T sfc[EPB * EF];
   __shared__ double sh2[EPB];  // per element: c * (-2/h)
+  __shared__ unsigned long long sg2[EPB];  // per element: the indicator's max |D rho|^2 (as bits)
   const T* fcomm = static_cast<const T*>(A.fcomm);
   T* trace_out = static_cast<T*>(A.trace_out);
   const int tid = threadIdx.x;
@@ -356,7 +359,10 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   // kernel drains; the common fluxes are read after it
   for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
   // c * (-2/h): 2^depth * (2/L) is exact, so this equals the rounded -2^(depth+1)/L times c
-  if (tid < ne) sh2[tid] = -A.c * (double(1ull << A.g.depth(A.keys[e0 + tid])) * A.twoL);
+  if (tid < ne) {
+    sh2[tid] = -A.c * (double(1ull << A.g.depth(A.keys[e0 + tid])) * A.twoL);
+    sg2[tid] = 0ull;
+  }
   __syncthreads();
   const int le = tid / N, i = tid % N;
   const bool act = le < ne;
@@ -462,6 +468,31 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
     }
   }
   __syncthreads();
+  if constexpr (std::is_same<T, double>::value) {
+    // the density-gradient indicator of the new state (FP64 form; the same arithmetic as the
+    // indicator kernel): eta = 2 max_i |D_xi rho|, flags from the thresholds
+    if (A.flags) {
+      if (act) {
+        const double* rho = su + le * EU;
+        double g2 = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          int qf, ia;
+          pt_split<DIM, NP>(i, a, &qf, &ia);
+          double d = 0.0;
+#pragma unroll
+          for (int j = 0; j < NP; ++j) d += ops.D[ia][j] * rho[line_pt<DIM, NP>(a, qf, j)];
+          g2 += d * d;
+        }
+        atomicMax(&sg2[le], static_cast<unsigned long long>(__double_as_longlong(g2)));  // g2 >= 0
+      }
+      __syncthreads();
+      if (act && i == 0) {
+        const double val = 2.0 * sqrt(__longlong_as_double(static_cast<long long>(sg2[le])));
+        A.flags[e0 + le] = int8_t(val > A.th_r ? 1 : (val < A.th_c ? -1 : 0));
+      }
+    }
+  }
   if (trace_out) {
     for (int k = tid; k < ne * EF; k += blockDim.x) {
       int le2 = k / EF, r = k % EF;

@@ -171,6 +171,10 @@ __global__ void __launch_bounds__(128) k_features(const double* __restrict__ u, 
 // flight, frees the tensor memory and ends the block.
 constexpr int TC_ROWS = 128, TC_TMEM_COLS = 64;
 constexpr long long TC_WAIT_CYCLES = 2000000000ll;
+// bound of the inference kernel's waits on its copies and MMAs (fr_tc_set_wait_limit); the drain
+// after a wait that gave up always uses TC_WAIT_CYCLES, so every copy and MMA in flight completes
+// before the block releases its shared and tensor memory
+long long g_fwd_wait_cycles = TC_WAIT_CYCLES;
 constexpr int TC_W1 = 0, TC_W2 = 8192, TC_W3 = 16384, TC_W4 = 24576, TC_A = 26624, TC_X0 = 43008;
 // shared-memory plan for `in` inputs: two staging buffers of 128*in BF16 (1024-byte granules),
 // then the biases, the three mbarriers and the TMEM address; plus 1024 bytes of alignment slack
@@ -190,7 +194,8 @@ __host__ __device__ inline TcPlan tc_plan(int in) {
 __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restrict__ P, int in,
                                                             const __nv_bfloat16* __restrict__ X, int64_t n,
                                                             float* __restrict__ logits,
-                                                            int8_t* __restrict__ flags, int* __restrict__ status) {
+                                                            int8_t* __restrict__ flags, int* __restrict__ status,
+                                                            long long wait_cycles) {
   extern __shared__ unsigned char sm_raw[];
   // 1024-byte aligned base for the operand tiles
   unsigned char* sm = sm_raw + ((1024 - (tc::smem_addr(sm_raw) & 1023)) & 1023);
@@ -252,7 +257,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
     const int nrow = int(n - row0 < TC_ROWS ? n - row0 : TC_ROWS);
     const unsigned char* xs;  // this tile's rows, contiguous BF16
     if (pend[b]) {
-      const bool ok = tc::mbar_wait(fb[b], fphase[b], TC_WAIT_CYCLES);
+      const bool ok = tc::mbar_wait(fb[b], fphase[b], wait_cycles);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -298,7 +303,7 @@ __global__ void __launch_bounds__(TC_ROWS) k_mlp_forward_tc(const float* __restr
         tc::commit(mb);
       }
       mma_pend = true;
-      const bool ok = tc::mbar_wait(mb, phase, TC_WAIT_CYCLES);
+      const bool ok = tc::mbar_wait(mb, phase, wait_cycles);
       if (__syncthreads_or(!ok)) {
         failed = true;
         break;
@@ -668,6 +673,8 @@ __global__ void k_adam(float* __restrict__ P, float* __restrict__ m, float* __re
 
 int mlp_param_count(int in) { return lay(in).total; }
 
+void mlp_set_wait_cycles(long long cycles) { g_fwd_wait_cycles = cycles > 0 ? cycles : TC_WAIT_CYCLES; }
+
 int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float* d_logits,
                 int8_t* d_flags, int* d_status, cudaStream_t s, Err* err) {
   if (in < 1 || in > 64) return set_error(err, FR_EINVAL, "the MLP takes 1..64 inputs");
@@ -696,7 +703,7 @@ int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float
   const int64_t ntiles = (n + TC_ROWS - 1) / TC_ROWS;
   const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
   k_mlp_forward_tc<<<grid, TC_ROWS, smem, s>>>(d_params, in, static_cast<const __nv_bfloat16*>(d_X), n,
-                                               d_logits, d_flags, d_status);
+                                               d_logits, d_flags, d_status, g_fwd_wait_cycles);
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -14,6 +14,8 @@ int mlp_features(int dim, int p, const double* u, const uint64_t* keys, int64_t 
                  int Dbase, double gamma, const DevOps& ops, void* d_X, cudaStream_t s, Err* err);
 // logits [n][3] and/or flags (argmax - 1) of n feature rows (1 <= in <= 64), on the tensor
 // cores; *d_status becomes nonzero if a tensor-core completion wait gave up
+// bound (clock cycles) of the inference kernel's completion waits; <= 0 restores the default
+void mlp_set_wait_cycles(long long cycles);
 int mlp_forward(const float* d_params, int in, const void* d_X, int64_t n, float* d_logits,
                 int8_t* d_flags, int* d_status, cudaStream_t s, Err* err);
 // cw[0..2] class weights (coarsen, keep, refine), cw[3] = 1 / (sum over the batch of w_label)

@@ -259,20 +259,38 @@ __global__ void k_indicator(const uint64_t* __restrict__ keys, int64_t M, KG g, 
 // Solution transfer (Sec. 4.2): copy; interpolation of the old (ancestor) polynomial at the new
 // points, with the Lagrange weights evaluated in the kernel; L2 projection of 2^dim fused
 // children with the tensor-product operators P (exact-quadrature mass and cross-mass matrices).
+// One thread per new point, 128 per block.  Without a mapping (src null) the block first maps
+// its own new leaves (one lower bound each, into shared memory), so the adaptation needs no
+// separate mapping kernel.
+constexpr int XFER_T = 128;
 template <int DIM, int NP>
-__global__ void k_transfer(KG g, const uint64_t* __restrict__ old_keys,
-                           const uint64_t* __restrict__ new_keys, const int32_t* __restrict__ src,
-                           const int8_t* __restrict__ tag, int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
-                           const __grid_constant__ DevOps ops, const double* __restrict__ uo,
-                           double* __restrict__ un) {
+__global__ void __launch_bounds__(XFER_T) k_transfer(KG g, const uint64_t* __restrict__ old_keys, int64_t n_old,
+                                                     const uint64_t* __restrict__ new_keys,
+                                                     const int32_t* __restrict__ src, const int8_t* __restrict__ tag,
+                                                     int32_t* bad, int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
+                                                     const __grid_constant__ DevOps ops, const double* __restrict__ uo,
+                                                     double* __restrict__ un) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
-  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= Mn_ub * S::N || (d_Mn && idx >= *d_Mn * S::N)) return;
-  int64_t j = idx / S::N;
-  int i = int(idx % S::N);
-  int64_t sidx = src[j];
-  int tg = tag[j];
+  constexpr int LMAX = XFER_T / S::N + 2;  // new leaves a block's points can touch
+  __shared__ int32_t s_src[LMAX];
+  __shared__ int8_t s_tag[LMAX];
+  const int64_t idx0 = int64_t(blockIdx.x) * XFER_T;
+  const int64_t Mn = (d_Mn && *d_Mn < Mn_ub) ? *d_Mn : Mn_ub;
+  const int64_t j0 = idx0 / S::N;
+  if (!src) {
+    const int t = threadIdx.x;
+    const int64_t jt = j0 + t;
+    if (t < LMAX && jt < Mn && jt * S::N < idx0 + XFER_T)
+      map_leaf<DIM>(old_keys, n_old, new_keys[jt], g, &s_src[t], &s_tag[t], bad);
+    __syncthreads();
+  }
+  const int64_t idx = idx0 + threadIdx.x;
+  if (idx >= Mn * S::N) return;
+  const int64_t j = idx / S::N;
+  const int i = int(idx % S::N);
+  const int64_t sidx = src ? src[j] : s_src[j - j0];
+  const int tg = src ? tag[j] : s_tag[j - j0];
   int ii[3] = {i % NP, (i / NP) % NP, DIM == 3 ? i / (NP * NP) : 0};
   if (tg == 0) {
 #pragma unroll
@@ -462,21 +480,22 @@ int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, d
 
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
                   cudaStream_t s, Err* err) {
-  if (prec == 1) return launch_traces_f32(dim, p, u, M, ops, tr, s, err);
-  if (prec == 2) return launch_traces_ff(dim, p, u, M, ops, tr, s, err);
+  if (prec >= 1 && prec <= 3) return launch_traces_f32(dim, p, u, M, ops, tr, s, err);
+  if (prec == 4) return launch_traces_ff(dim, p, u, M, ops, tr, s, err);
   return launch_traces_f64(dim, p, u, M, ops, tr, s, err);
 }
 
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {
-  if (prec == 1) return launch_faces_f32(dim, p, A, ops, s, err);
-  if (prec == 2) return launch_faces_ff(dim, p, A, ops, s, err);
+  if (prec >= 1 && prec <= 3) return launch_faces_f32(dim, p, A, ops, s, err);
+  if (prec == 4) return launch_faces_ff(dim, p, A, ops, s, err);
   return launch_faces_f64(dim, p, A, ops, s, err);
 }
 
 int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s,
                  Err* err) {
   if (prec == 1) return launch_stage_f32(dim, p, A, ops, s, err);
-  if (prec == 2) return launch_stage_ff(dim, p, A, ops, s, err);
+  if (prec == 2 || prec == 3) return launch_stage_tc(prec, dim, p, A, ops, s, err);
+  if (prec == 4) return launch_stage_ff(dim, p, A, ops, s, err);
   return launch_stage_f64(dim, p, A, ops, s, err);
 }
 
@@ -491,13 +510,13 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
   return 0;
 }
 
-int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
-                    const int32_t* src, const int8_t* tag, int64_t M_new, const int64_t* d_M_new,
+int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64_t n_old, const uint64_t* new_keys,
+                    const int32_t* src, const int8_t* tag, int32_t* bad, int64_t M_new, const int64_t* d_M_new,
                     const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err) {
   if (M_new <= 0) return 0;
   int64_t T = M_new * ipow(p + 1, dim);
-  FR_DISPATCH(dim, p, (launch_dependent(k_transfer<DD, NN>, nb_of(T, 128), 128, s, g, old_keys, new_keys, src, tag, M_new,
-                                        d_M_new, ops, u_old, u_new)));
+  FR_DISPATCH(dim, p, (launch_dependent(k_transfer<DD, NN>, nb_of(T, XFER_T), XFER_T, s, g, old_keys, n_old, new_keys,
+                                        src, tag, bad, M_new, d_M_new, ops, u_old, u_new)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

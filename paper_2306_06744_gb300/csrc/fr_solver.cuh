@@ -25,13 +25,17 @@ struct StageArgs {
   int64_t M;
   KG g;
   double twoL, gamma, a, b, c;  // twoL = 2 / L
+  int* status;                  // device word set by a tensor-core kernel whose completion wait gave up
+  int8_t* flags;                // FP64 form: density-gradient flags of out (nullable)
+  double th_r, th_c;            // their refine / coarsen thresholds
 };
 
 struct Mesh;  // defined in fr_api.cu
 
 int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
                  const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err);
-// prec: 0 FP64, 1 FP32 with FP64 Runge-Kutta combination, 2 double-word (two floats)
+// prec: 0 FP64, 1 FP32 with FP64 Runge-Kutta combination, 2 TF32 and 3 bf16x3 tensor-core
+// derivative (otherwise as 1; 3D p = 3), 4 double-word (two floats)
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
                   cudaStream_t s, Err* err);
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
@@ -48,14 +52,17 @@ int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops
 FR_DECLARE_PREC(f64)
 FR_DECLARE_PREC(f32)
 FR_DECLARE_PREC(ff)
+// element stage of the tensor-core forms (fr_tc_stage.cu)
+int launch_stage_tc(int prec, int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, Err* err);
 // indicator: mode 0 density gradient, 1 analytic centre; flags int8[M], eta double[M] (nullable)
 int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double t,
                      const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
                      const DevOps& ops, const double* u, int8_t* flags, double* eta,
                      cudaStream_t s, Err* err);
-// d_M_new (nullable): device count of new leaves, M_new then an upper bound
-int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, const uint64_t* new_keys,
-                    const int32_t* src, const int8_t* tag, int64_t M_new, const int64_t* d_M_new,
+// d_M_new (nullable): device count of new leaves, M_new then an upper bound.  src/tag: the
+// old->new mapping, or null: the kernel maps the new leaves itself (mapping failures set *bad)
+int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64_t n_old, const uint64_t* new_keys,
+                    const int32_t* src, const int8_t* tag, int32_t* bad, int64_t M_new, const int64_t* d_M_new,
                     const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err);
 // norms: out[0] = sum w|J|(rho_ex-rho)^2, out[1..nv] integrals, out[nv+1] min rho, out[nv+2] min p
 int launch_norms(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,

@@ -63,11 +63,21 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
 }
 
 // waits for the completion of the phase with the given parity; gives up after `limit` clock
-// cycles and returns false
+// cycles and returns false.  Each round first tests without blocking, then checks the clock, then
+// waits with try_wait (which may suspend the thread for a while inside the instruction), so a
+// limit shorter than the completion's latency is honoured.
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > limit) return false;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
@@ -75,7 +85,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long l
         : "r"(mbar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > limit) return false;
   }
 }
 

@@ -361,6 +361,193 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
   }
 }
 
+// ---- balance pass issued without host synchronisation: generate -> sort -> merge ----
+// The octants of a pass are placed by a warp-aggregated atomic counter: their order does not
+// matter, because they are sorted next and equal keys are indistinguishable, so the tree stays
+// bit-exact.  The sort kernel, which holds the whole sorted set, also computes where every leaf
+// lands in the merged tree: a leaf that holds octants becomes its k >= 1 linearised octants, so
+// the leaves before it shift by the sum of (k - 1) over the leaves holding octants before it,
+// P[r] = sum over the sorted octants s < r of (kept(s) - first octant of its leaf(s)).  The merge
+// then needs no count and no scan over the leaves.
+template <int DIM>
+__global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl, int64_t n_ub, KG g,
+                               int D, uint64_t* __restrict__ out, int64_t cap) {
+  pdl_wait_then_release();
+  constexpr int LPL = BalLanes<DIM>::value;
+  const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t i = gt / LPL;
+  const int o = int(gt % LPL);
+  const int64_t n = ctl[CTL_OVER] == 0 ? ctl[CTL_N] : 0;
+  uint32_t N[3];
+  int dA = 0;
+  const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA) : 0;
+  // every lane of the warp takes part: inclusive prefix of the counts, one atomic per warp
+  const int lane = int(threadIdx.x & 31);
+  int incl = c;
+#pragma unroll
+  for (int w = 1; w < 32; w <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, w);
+    if (lane >= w) incl += y;
+  }
+  const int tot = __shfl_sync(0xffffffffu, incl, 31);
+  unsigned long long base = 0;
+  if (lane == 31 && tot > 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(ctl + CTL_G), (unsigned long long)tot);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (c == 0) return;
+  int64_t q = int64_t(base) + (incl - c);
+  const uint64_t rawN = interleave<DIM>(N);
+  for (int l = dA + 1; l <= D - 1; ++l) {
+    const uint64_t span = vol_raw<DIM>(g, l - 1);
+    const uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
+    for (int ch = 0; ch < (1 << DIM); ++ch, ++q)
+      if (q < cap) out[q] = child_key<DIM>(g, anc, ch);  // past the capacity: counted, not stored
+  }
+}
+
+// one block: sorts the pass's octants, computes the merge shifts P[0..nS] and the merged leaf
+// count, and prepares the control block for the merge (CTL_NPREV, CTL_GS) and the next pass
+// (CTL_G zeroed).  An oversized pass, or any pass after one, merges nothing.
+template <int DIM>
+__global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, int64_t* __restrict__ ctl,
+                                                     int64_t cap, int D, const uint64_t* __restrict__ k, KG g,
+                                                     int32_t* __restrict__ P) {
+  pdl_wait_then_release();
+  __shared__ uint64_t sk[SMALL_SORT_MAX];
+  __shared__ int32_t wsum[32];
+  const int t = threadIdx.x;
+  const int64_t n = ctl[CTL_N];
+  const int64_t G = ctl[CTL_G];
+  const bool over = ctl[CTL_OVER] != 0 || G > cap || G > SMALL_SORT_MAX;
+  __syncthreads();  // every thread has read the control block before thread 0 rewrites it
+  if (over || G == 0) {
+    if (t == 0) {
+      if (ctl[CTL_OVER] == 0 && G > 0) ctl[CTL_OVER] = D;
+      ctl[CTL_NPREV] = n;
+      ctl[CTL_GS] = 0;
+      ctl[CTL_G] = 0;
+    }
+    return;
+  }
+  const int nS = int(G);
+  if (nS <= RANK_SORT_MAX) {
+    // rank sort: each key's position is the number of smaller keys plus the equal keys before it
+    uint64_t mine = 0;
+    if (t < nS) mine = sk[t] = S[t];
+    __syncthreads();
+    if (t < nS) {
+      int r = 0;
+      for (int j = 0; j < nS; ++j) {
+        const uint64_t o = sk[j];
+        r += (o < mine) || (o == mine && j < t);
+      }
+      S[r] = mine;
+    }
+  } else {
+    int Pw = 1;
+    while (Pw < nS) Pw <<= 1;
+    for (int i = t; i < Pw; i += blockDim.x) sk[i] = i < nS ? S[i] : ~0ull;
+    __syncthreads();
+    for (int kk = 2; kk <= Pw; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = t; i < Pw; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) {
+            const uint64_t a = sk[i], b = sk[l];
+            const bool up = (i & kk) == 0;
+            if ((a > b) == up) {
+              sk[i] = b;
+              sk[l] = a;
+            }
+          }
+        }
+        const int next_j = j > 1 ? j >> 1 : kk;
+        if (j >= 32 || next_j >= 32)
+          __syncthreads();
+        else
+          __syncwarp();
+      }
+    }
+    for (int i = t; i < nS; i += blockDim.x) S[i] = sk[i];
+  }
+  __syncthreads();  // the sorted octants are in S (global writes of this block are visible now)
+  // per thread 4 consecutive octants r = 4t .. 4t+3: kept(r) - first(r), with first(r) when the
+  // containing leaf of r differs from that of r - 1
+  int v[4], sum = 0;
+  int64_t prev_leaf = -1;
+  if (4 * t < nS && 4 * t > 0) prev_leaf = upper_bound_dev(k, n, S[4 * t - 1]) - 1;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = 4 * t + q;
+    v[q] = 0;
+    if (r < nS) {
+      const int64_t leaf = upper_bound_dev(k, n, S[r]) - 1;
+      v[q] = int(lin_keep<DIM>(S, nS, g, r)) - int(leaf != prev_leaf);
+      prev_leaf = leaf;
+    }
+    sum += v[q];
+  }
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = t & 31, wid = t >> 5;
+  int incl = sum;
+#pragma unroll
+  for (int w = 1; w < 32; w <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, w);
+    if (lane >= w) incl += y;
+  }
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    const int x = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+    int wi = x;
+#pragma unroll
+    for (int w = 1; w < 32; w <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, wi, w);
+      if (lane >= w) wi += y;
+    }
+    wsum[lane] = wi - x;  // exclusive prefix of the warp totals
+  }
+  __syncthreads();
+  int run = wsum[wid] + incl - sum;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = 4 * t + q;
+    if (r < nS) P[r] = run;
+    run += v[q];
+    if (r == nS - 1) {
+      P[nS] = run;  // total shift: the merged tree holds n + P[nS] leaves
+      ctl[CTL_NPREV] = n;
+      ctl[CTL_N] = n + run;
+      ctl[CTL_GS] = nS;
+      ctl[CTL_G] = 0;
+      ctl[CTL_PASSES] += 1;
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_merge_fast(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl, int64_t n_ub,
+                             const uint64_t* __restrict__ S, const int32_t* __restrict__ P, KG g,
+                             uint64_t* __restrict__ out) {
+  pdl_wait_then_release();
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n_ub || i >= ctl[CTL_NPREV]) return;
+  const int64_t nS = ctl[CTL_GS];
+  const uint64_t key = k[i];
+  if (nS == 0) {
+    out[i] = key;
+    return;
+  }
+  const int64_t lo = lower_bound_dev(S, nS, key);
+  const int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
+  int64_t o = i + P[lo];
+  if (hi == lo) {
+    out[o] = key;
+    return;
+  }
+  for (int64_t r = lo; r < hi; ++r)
+    if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
+}
+
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
 template <int DIM>
 __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64_t* __restrict__ nw,
@@ -369,88 +556,86 @@ __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64
   pdl_wait_then_release();
   int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (j >= nn_ub || (d_nn && j >= *d_nn)) return;
-  uint64_t key = nw[j];
-  int64_t B = lower_bound_dev(old, no, key);
-  if (B < no && old[B] == key) {
-    src[j] = int32_t(B);
-    tag[j] = 0;
-  } else if (B > 0 && is_ancestor<DIM>(g, old[B - 1], key)) {
-    src[j] = int32_t(B - 1);
-    tag[j] = 1;
-  } else {
-    // the old leaves must be exactly the 2^dim children of the new leaf; otherwise the tree
-    // pair is invalid: report it and emit an in-bounds copy so later kernels stay in bounds
-    bool ok = B + (1 << DIM) <= no;
-    for (int c = 0; c < (1 << DIM) && ok; ++c) ok = old[B + c] == child_key<DIM>(g, key, c);
-    if (ok) {
-      src[j] = int32_t(B);
-      tag[j] = 2;
-    } else {
-      atomicExch(bad, 1);
-      src[j] = int32_t(B < no ? B : no - 1);
-      tag[j] = 0;
-    }
-  }
+  map_leaf<DIM>(old, no, nw[j], g, src + j, tag + j, bad);
 }
 
 // Face connectivity (Sec. 3.3): same-depth face-neighbour box, point location of its anchor.
 template <int DIM>
 __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64_t* __restrict__ d_n, KG g,
                        int32_t* __restrict__ nbr, int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
-                       int32_t* __restrict__ contrib, int32_t* bad) {
+                       int32_t* __restrict__ contrib, int32_t* bad, int64_t* __restrict__ fcnt) {
   pdl_wait_then_release();
   constexpr int NFC = 2 * DIM;
-  int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= n_ub * NFC) return;
+  // with fcnt: the block holds whole leaves (blockDim a multiple of 2*dim) and also writes each
+  // leaf's face-list counts, conforming faces it owns (its + faces) low, coarse sides of hanging
+  // faces high; leaves past the count get zero
+  __shared__ int s_cnt[2 * 256 / NFC + 2];
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n = d_n ? *d_n : n_ub;
-  if (t >= n * NFC) return;
-  int64_t e = t / NFC;
-  int f = int(t % NFC), axis = f >> 1, side = f & 1;
-  uint64_t key = k[e];
-  int d = g.depth(key);
-  uint32_t x[3], N[3];
-  deinterleave<DIM>(g.raw(key), x);
-  uint32_t w = g.width(d), mask = (g.Dmax >= 32) ? 0xFFFFFFFFu : ((1u << g.Dmax) - 1u);
-  for (int a = 0; a < DIM; ++a) N[a] = x[a];
-  N[axis] = (x[axis] + (side ? w : (0u - w))) & mask;
-  uint64_t kN = g.make(interleave<DIM>(N), d);
-  int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
-  if (j < 0) j = 0;
-  uint64_t kj = k[j];
-  int dj = g.depth(kj);
-  if (kj == kN) {
-    nbr[t] = int32_t(j);
-    ftype[t] = 0;
-    slot[t] = -1;
-  } else if (dj < d) {
-    if (dj != d - 1) atomicExch(bad, 1);
-    nbr[t] = int32_t(j);
-    ftype[t] = 1;
-    int c = child_index<DIM>(g, key), s = 0, sh = 0;
-    for (int b = 0; b < DIM; ++b)
-      if (b != axis) s |= ((c >> b) & 1) << sh++;
-    slot[t] = int8_t(s);
-  } else {
-    ftype[t] = 2;
-    slot[t] = 0;
-    int first = -1;
-    for (int c = 0; c < (1 << DIM); ++c) {
-      if (((c >> axis) & 1) != (side ? 0 : 1)) continue;
-      uint64_t kc = child_key<DIM>(g, kN, c);
-      int64_t m = lower_bound_dev(k, n, kc);
-      if (m >= n || k[m] != kc) {
-        atomicExch(bad, 1);
-        m = 0;
-      }
-      int s = 0, sh = 0;
+  const int lt = int(threadIdx.x) / NFC;
+  if (fcnt && int(threadIdx.x) % NFC == 0) s_cnt[2 * lt] = s_cnt[2 * lt + 1] = 0;
+  if (fcnt) __syncthreads();
+  const bool act = t < n_ub * NFC && t < n * NFC;
+  int type = -1;
+  const int f = int(t % NFC);
+  if (act) {
+    const int64_t e = t / NFC;
+    const int axis = f >> 1, side = f & 1;
+    const uint64_t key = k[e];
+    const int d = g.depth(key);
+    uint32_t x[3], N[3];
+    deinterleave<DIM>(g.raw(key), x);
+    const uint32_t w = g.width(d), mask = (g.Dmax >= 32) ? 0xFFFFFFFFu : ((1u << g.Dmax) - 1u);
+    for (int a = 0; a < DIM; ++a) N[a] = x[a];
+    N[axis] = (x[axis] + (side ? w : (0u - w))) & mask;
+    const uint64_t kN = g.make(interleave<DIM>(N), d);
+    int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
+    if (j < 0) j = 0;
+    const uint64_t kj = k[j];
+    const int dj = g.depth(kj);
+    if (kj == kN) {
+      nbr[t] = int32_t(j);
+      ftype[t] = 0;
+      slot[t] = -1;
+      type = 0;
+    } else if (dj < d) {
+      if (dj != d - 1) atomicExch(bad, 1);
+      nbr[t] = int32_t(j);
+      ftype[t] = 1;
+      int c = child_index<DIM>(g, key), sl = 0, sh = 0;
       for (int b = 0; b < DIM; ++b)
-        if (b != axis) s |= ((c >> b) & 1) << sh++;
-      if (s == 0) first = int(m);
-      if (contrib) contrib[t * 4 + s] = int32_t(m);
+        if (b != axis) sl |= ((c >> b) & 1) << sh++;
+      slot[t] = int8_t(sl);
+      type = 1;
+    } else {
+      ftype[t] = 2;
+      slot[t] = 0;
+      type = 2;
+      int first = -1;
+      for (int c = 0; c < (1 << DIM); ++c) {
+        if (((c >> axis) & 1) != (side ? 0 : 1)) continue;
+        uint64_t kc = child_key<DIM>(g, kN, c);
+        int64_t m = lower_bound_dev(k, n, kc);
+        if (m >= n || k[m] != kc) {
+          atomicExch(bad, 1);
+          m = 0;
+        }
+        int sl = 0, sh = 0;
+        for (int b = 0; b < DIM; ++b)
+          if (b != axis) sl |= ((c >> b) & 1) << sh++;
+        if (sl == 0) first = int(m);
+        if (contrib) contrib[t * 4 + sl] = int32_t(m);
+      }
+      if (contrib && DIM == 2) contrib[t * 4 + 2] = contrib[t * 4 + 3] = -1;  // 2 contributors in 2D
+      nbr[t] = first;
     }
-    if (contrib && DIM == 2) contrib[t * 4 + 2] = contrib[t * 4 + 3] = -1;  // 2 contributors in 2D
-    nbr[t] = first;
   }
+  if (!fcnt) return;
+  if ((f & 1) && type == 0) atomicAdd(&s_cnt[2 * lt], 1);
+  if (type == 2) atomicAdd(&s_cnt[2 * lt + 1], 1);
+  __syncthreads();
+  const int64_t e = t / NFC;
+  if (f == 0 && e < n_ub) fcnt[e] = int64_t(s_cnt[2 * lt]) | (int64_t(s_cnt[2 * lt + 1]) << 32);
 }
 
 template <int DIM>
@@ -780,27 +965,37 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
                        int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err) {
-  Buf<uint64_t> gen, tmp, out;
+  Buf<uint64_t> gen, out;
   int rc = 0;
+  const int64_t cap = SMALL_SORT_MAX;
   for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
     Scratch S(&A);
     const int64_t nb = *n_ub;
-    int32_t* cnt = S.get<int32_t>(nb);
-    int64_t* offs = S.get<int64_t>(nb);
-    if (!cnt || !offs) {
+    int32_t* P = S.get<int32_t>(cap + 1);
+    if (!P || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap))) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g, D, cnt)));
+    DIM_DISPATCH(dim, (launch_dependent(k_bal_gen_fast<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g,
+                                        D, gen.p, cap)));
     ++launch_counter();
-    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    Offs O;
-    if ((rc = scan_counts_local(cnt, offs, nb, d_ctl + CTL_G, S, s, err, &O))) break;
-    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, nb, -1, SMALL_SORT_MAX, O, A, s, err))) break;
-    *n_ub = nb + SMALL_SORT_MAX;
+    DIM_DISPATCH(dim, (launch_dependent(k_sort_annot<D_>, 1, 1024, s, gen.p, d_ctl, cap, D,
+                                        static_cast<const uint64_t*>(keys.p), g, P)));
+    ++launch_counter();
+    DIM_DISPATCH(dim, (launch_dependent(k_merge_fast<D_>, nblk(nb), TB, s, static_cast<const uint64_t*>(keys.p),
+                                        static_cast<const int64_t*>(d_ctl), nb, static_cast<const uint64_t*>(gen.p),
+                                        static_cast<const int32_t*>(P), g, out.p)));
+    ++launch_counter();
+    if (cudaGetLastError() != cudaSuccess) {
+      rc = set_error(err, FR_ECUDA, "balance pass launch");
+      break;
+    }
+    Buf<uint64_t> t = keys;  // the merged tree becomes the tree
+    keys = out;
+    out = t;
+    *n_ub = nb + cap;
   }
   gen.release(A);
-  tmp.release(A);
   out.release(A);
   return rc;
 }
@@ -815,10 +1010,13 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
 }
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
-              Err* err) {
+              Err* err, int64_t* d_fcnt) {
   if (n <= 0) return 0;
-  int64_t T = n * 2 * dim;
-  DIM_DISPATCH(dim, (launch_dependent(k_conn<D_>, nblk(T), TB, s, d_keys, n, d_n, g, d_nbr, d_ftype, d_slot, d_contrib, d_bad)));
+  const int64_t T = n * 2 * dim;
+  // blocks of whole leaves: 64 leaves (2D, 256 threads) or 32 (3D, 192 threads)
+  const int bt = dim == 2 ? 256 : 192;
+  DIM_DISPATCH(dim, (launch_dependent(k_conn<D_>, nblk(T, bt), bt, s, d_keys, n, d_n, g, d_nbr, d_ftype, d_slot,
+                                      d_contrib, d_bad, d_fcnt)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -75,7 +75,8 @@ EXPORTS = ["fr_mesh_init", "fr_mesh_free", "fr_step", "fr_run", "fr_adapt", "fr_
            "fr_keys_sort", "fr_keys_linearise", "fr_tree_balance", "fr_tree_adapt", "fr_tree_map",
            "fr_tree_conn", "fr_profile_enable", "fr_profile_read", "fr_kernel_launches",
            "fr_keys_sort_noalloc", "fr_tree_complete", "fr_mlp_param_count", "fr_features",
-           "fr_set_learned_indicator", "fr_mlp_forward", "fr_mlp_grad", "fr_mlp_train_step"]
+           "fr_set_learned_indicator", "fr_mlp_forward", "fr_mlp_grad", "fr_mlp_train_step",
+           "fr_tc_set_wait_limit"]
 NOALLOC_SORT_MAX_KEYS = 1 << 18
 
 
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = True):
     lib.fr_mlp_train_step.argtypes = [C.c_int, vp, vp, vp, i64, vp, vp, i64, vp, C.c_float, vp, vp]
     lib.fr_profile_enable.argtypes = [vp, C.c_int]
     lib.fr_profile_read.argtypes = [vp, C.POINTER(FRProfile)]
+    lib.fr_tc_set_wait_limit.argtypes = [C.c_longlong]
+    lib.fr_tc_set_wait_limit.restype = None
     lib.fr_kernel_launches.restype = C.c_int64
     lib.fr_kernel_launches.argtypes = []
     _lib = lib
@@ -401,6 +404,11 @@ def mlp_forward(params, X, stream=None):
                                  C.c_void_p(logits.data_ptr()), C.c_void_p(flags.data_ptr()),
                                  _stream_handle(stream)))
     return logits, flags
+
+
+def tc_set_wait_limit(cycles: int) -> None:
+    """Bound (clock cycles) of the tensor-core inference kernel's completion waits; <= 0: default."""
+    load().fr_tc_set_wait_limit(int(cycles))
 
 
 def mlp_grad(params, X, y, class_w, stream=None):

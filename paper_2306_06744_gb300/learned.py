@@ -142,7 +142,7 @@ def experiment(steps: int = 120, snapshots: int = 30, log=print) -> dict:
 
     import torch
     cfg4 = W.config("vortex3d_p3_multi")
-    cfg3 = dict(W.config("vortex3d_p2_tube"), precision=2,
+    cfg3 = dict(W.config("vortex3d_p2_tube"), precision=4,
                 th_refine=cfg4["th_refine"], th_coarsen=cfg4["th_coarsen"])
     t0 = time.perf_counter()
     X, y = collect_pairs(cfg3, snapshots=snapshots, horizon=20, every=10)
@@ -160,7 +160,7 @@ def experiment(steps: int = 120, snapshots: int = 30, log=print) -> dict:
     torch.cuda.empty_cache()
     res["plain_f64_every10"] = deploy_run(dict(cfg4, precision=0, indicator=0), steps, 10)
     res["learned_f64_every30"] = deploy_run(dict(cfg4, precision=0, indicator=3), steps, 30, params)
-    res["learned_double_word_every30"] = deploy_run(dict(cfg4, precision=2, indicator=3), steps, 30,
+    res["learned_double_word_every30"] = deploy_run(dict(cfg4, precision=4, indicator=3), steps, 30,
                                                     params)
     return res
 

@@ -17,7 +17,7 @@ def _cfg(name, **kw):
     return c
 
 
-@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("prec", [0, 4])
 def test_3d_steps_with_adaptation(prec):
     cfg = _cfg("vortex3d_p2_tube", Dbase=2, Dmax=4, th_refine=0.02, th_coarsen=0.005)
     g = fr.Mesh(dict(cfg, precision=prec))

@@ -123,3 +123,25 @@ def test_features_parity_and_indicator_modes():
     want_keys = fr.tree_adapt(3, cfg["Dbase"], cfg["Dmax"], keys0, flags.cpu().numpy())
     g.adapt()
     assert np.array_equal(g.leaves(), want_keys)
+
+
+def test_forward_wait_timeout_is_reported_and_device_stays_usable():
+    # the inference kernel's completion waits are bounded; with the bound set below an MMA's
+    # latency the waits give up, the blocks drain what they issued (default bound) and free their
+    # tensor memory, and the call reports FR_ETIMEOUT; with the default bound restored the next
+    # call on the same device matches the oracle
+    import torch
+    n_in, n = 55, 20000
+    P = _rand_params(n_in, 5)
+    Xd, Xh = _rand_X(n, n_in, 6)
+    Pd = torch.from_numpy(P).cuda()
+    fr.tc_set_wait_limit(1)
+    try:
+        with pytest.raises(fr.FRError) as e:
+            fr.mlp_forward(Pd, Xd)
+        assert e.value.code == fr.FR_ETIMEOUT
+    finally:
+        fr.tc_set_wait_limit(0)
+    logits, _ = fr.mlp_forward(Pd, Xd)
+    want, _ = mlp.forward(P, Xh, bf16_round=True)
+    assert np.abs(logits.cpu().numpy() - want).max() < 1e-2 * np.abs(want).max()
