@@ -374,19 +374,27 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   int32_t hb[2] = {0, 0}, hs = 0;
   Buf<uint64_t> nk;
   Buf<double> nu;
-  Buf<int32_t> hcon;
+  Buf<int32_t> src, hcon;
+  Buf<int8_t> tag;
   bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
   int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
     int r = 0;
     if (transfer) {
-      // the mapping (Sec. 4.2) runs inside the transfer kernel, block by block
+      // small meshes (issued without synchronisation, where launches set the cost): the mapping
+      // (Sec. 4.2) runs inside the transfer kernel, block by block; large meshes map first with
+      // one thread per new leaf, which keeps the transfer's blocks off the search latency
+      if (!fast) {
+        if (!r) r = src.ensure(m->A, nb);
+        if (!r) r = tag.ensure(m->A, nb);
+        if (!r) r = tree_map(m->dim, m->g, m->keys.p, M0, nk.p, nb, d_n, src.p, tag.p, bad + 1, s, err);
+      }
       T.mark(1);
       if (!r) r = nu.ensure(m->A, size_t(nb) * m->EU);
       if (!r)
-        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, nullptr, nullptr, bad + 1, nb, d_n, m->ops,
-                            m->u.p, nu.p, s, err);
+        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, fast ? nullptr : src.p, fast ? nullptr : tag.p,
+                            bad + 1, nb, d_n, m->ops, m->u.p, nu.p, s, err);
     } else {
       T.mark(1);
     }
@@ -426,6 +434,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   if (!rc && !fast) rc = rest(h_ctl[CTL_N], nullptr);
   if (!rc) rc = conn_check(m, hb);
   const int64_t M1 = h_ctl[CTL_N];
+  src.release(m->A);
+  tag.release(m->A);
   if (!rc) {
     // the time-step buffers for the new size, while the mesh still holds the old tree (a block
     // that is released and not replaced here is grown again by ready_buffers)

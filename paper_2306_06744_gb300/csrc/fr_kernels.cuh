@@ -354,18 +354,29 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   const int tid = threadIdx.x;
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
   const int ne = int((A.M - e0) < EPB ? (A.M - e0) : EPB);
-  // the stage's input state and the keys come from earlier launches than the interface kernel
-  // this one depends on, so they are read, and the pointwise fluxes formed from them, while that
-  // kernel drains; the common fluxes are read after it
-  for (int k = tid; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(A.us[e0 * EU + k]);
+  // the stage's input state, the state at the start of the step and the keys come from earlier
+  // launches than the interface kernel this one depends on, so they are read, and the pointwise
+  // fluxes formed from them, while that kernel drains; the common fluxes are read after it.  Each
+  // thread loads its own point; the FP64 values of u_s (FP32 form) and u^n stay in registers for
+  // the Runge-Kutta combination.
+  const int le = tid / N, i = tid % N;
+  const bool act = le < ne;
+  double usr[NV], unr[NV];
+  if (act) {
+    const int64_t b0 = (e0 + le) * EU + i;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      usr[v] = A.us[b0 + v * N];
+      unr[v] = A.a != 0.0 ? A.un[b0 + v * N] : 0.0;
+      su[le * EU + v * N + i] = Ar<T>::from_d(usr[v]);
+    }
+  }
   // c * (-2/h): 2^depth * (2/L) is exact, so this equals the rounded -2^(depth+1)/L times c
   if (tid < ne) {
     sh2[tid] = -A.c * (double(1ull << A.g.depth(A.keys[e0 + tid])) * A.twoL);
     sg2[tid] = 0ull;
   }
   __syncthreads();
-  const int le = tid / N, i = tid % N;
-  const bool act = le < ne;
   const T gm1 = cst<T>(A.gamma - 1.0), ngmh = cst<T>(-0.5 * (A.gamma - 1.0));
   RT outv[NV];
   if (act) {
@@ -432,17 +443,14 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       for (int v = 0; v < NV; ++v) R[v] = fma_t(ops.gLh[ia], Fm[v * NF], fma_t(ops.gRh[ia], Fp[v * NF], R[v]));
     }
     const double cs = sh2[le];
-    const int64_t base = (e0 + le) * EU + i;
     if constexpr (!std::is_same<T, ff>::value) {
       // FP64 combination (native FP64 and the mixed FP32 form); b = 1 (first stage) skips the
       // product, which is exact there
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        // u_s: the staged copy when it is exact (FP64), else the FP64 state in memory
-        const double us = std::is_same<T, double>::value ? Ar<T>::to_d(su[le * EU + v * N + i])
-                                                         : A.us[base + v * N];
+        const double us = usr[v];
         double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? us : A.b * us);
-        if (A.a != 0.0) o = fma(A.a, A.un[base + v * N], o);
+        if (A.a != 0.0) o = fma(A.a, unr[v], o);
         outv[v] = o;
       }
     } else {
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         ff o = fma_t(bb, su[le * EU + v * N + i], cc * R[v]);
-        if (A.a != 0.0) o = fma_t(aa, ff_from_double(A.un[base + v * N]), o);
+        if (A.a != 0.0) o = fma_t(aa, ff_from_double(unr[v]), o);
         outv[v] = o;
       }
     }
@@ -494,15 +502,24 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
     }
   }
   if (trace_out) {
-    for (int k = tid; k < ne * EF; k += blockDim.x) {
-      int le2 = k / EF, r = k % EF;
-      int f = r / (NV * NF), v = (r / NF) % NV, qq = r % NF;
+    // one thread per (element, face, face point), all variables from one set of indices
+    constexpr int FQ = S::NFC * NF;
+    for (int k = tid; k < ne * FQ; k += blockDim.x) {
+      const int le2 = k / FQ, r = k % FQ;
+      const int f = r / NF, qq = r % NF;
       const T* lf = (f & 1) ? ops.lp : ops.lm;
-      const T* ue = su + le2 * EU + v * N;
-      T s = zero_t<T>();
+      int pts[NP];
 #pragma unroll
-      for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[line_pt<DIM, NP>(f >> 1, qq, j)], s);
-      trace_out[e0 * EF + k] = s;
+      for (int j = 0; j < NP; ++j) pts[j] = line_pt<DIM, NP>(f >> 1, qq, j);
+      T* to = trace_out + (e0 + le2) * EF + f * NV * NF + qq;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const T* ue = su + le2 * EU + v * N;
+        T s = zero_t<T>();
+#pragma unroll
+        for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[pts[j]], s);
+        to[v * NF] = s;
+      }
     }
   }
 }

@@ -314,15 +314,23 @@ __global__ void __launch_bounds__(TS_T) k_stage_tc(StageArgs A, const __grid_con
   __syncthreads();
   float* trace_out = static_cast<float*>(A.trace_out);
   if (trace_out) {
-    for (int k = tid; k < ne * TS_EF; k += TS_T) {
-      const int le = k / TS_EF, r = k % TS_EF;
-      const int f = r / (TS_NV * TS_NF), v = (r / TS_NF) % TS_NV, qq = r % TS_NF;
+    // one thread per (element, face, face point), all variables from one set of indices
+    for (int k = tid; k < ne * 6 * TS_NF; k += TS_T) {
+      const int le = k / (6 * TS_NF), r = k % (6 * TS_NF);
+      const int f = r / TS_NF, qq = r % TS_NF;
       const float* lf = (f & 1) ? ops.lp : ops.lm;
-      const float* ue = su + le * TS_EU + v * TS_N;
-      float s = 0.f;
+      int pts[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) s = fmaf(lf[j], ue[line_pt<3, 4>(f >> 1, qq, j)], s);
-      trace_out[e0 * TS_EF + k] = s;
+      for (int j = 0; j < 4; ++j) pts[j] = line_pt<3, 4>(f >> 1, qq, j);
+      float* to = trace_out + (e0 + le) * TS_EF + f * TS_NV * TS_NF + qq;
+#pragma unroll
+      for (int v = 0; v < TS_NV; ++v) {
+        const float* ue = su + le * TS_EU + v * TS_N;
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s = fmaf(lf[j], ue[pts[j]], s);
+        to[v * TS_NF] = s;
+      }
     }
   }
 }

@@ -133,7 +133,7 @@ struct Nofs {
 
 template <int DIM>
 __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_t n, const KG& g,
-                                          int D, int64_t i, int o, uint32_t* N, int* dA) {
+                                          int D, int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr) {
   uint64_t key = k[i];
   if (g.depth(key) != D) return false;
   int oo = o < (DIM == 2 ? 4 : 13) ? o : o + 1;  // skip the centre of the 3^dim stencil
@@ -147,6 +147,7 @@ __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_
   int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
   if (j < 0) j = 0;  // only on an incomplete tree, which callers reject beforehand
   *dA = g.depth(k[j]);
+  if (jA) *jA = j;
   return *dA < D - 1;
 }
 
@@ -173,10 +174,10 @@ struct BalLanes {
 // number of octants lane (i, o) generates, with the containing leaf's depth and the box
 template <int DIM>
 __device__ __forceinline__ int bal_lane(const uint64_t* __restrict__ k, int64_t n, const KG& g, int D,
-                                        int64_t i, int o, uint32_t* N, int* dA) {
+                                        int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr) {
   constexpr int NO = Nofs<DIM>::value;
   if (i >= n || o >= NO) return 0;
-  return bal_query<DIM>(k, n, g, D, i, o, N, dA) ? (D - 1 - *dA) << DIM : 0;
+  return bal_query<DIM>(k, n, g, D, i, o, N, dA, jA) ? (D - 1 - *dA) << DIM : 0;
 }
 
 template <int DIM>
@@ -369,9 +370,14 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
 // the leaves before it shift by the sum of (k - 1) over the leaves holding octants before it,
 // P[r] = sum over the sorted octants s < r of (kept(s) - first octant of its leaf(s)).  The merge
 // then needs no count and no scan over the leaves.
+// With `packed` (when the key's bits and PACK_BITS fit 64), each octant is stored as
+// key << PACK_BITS | index of the leaf that contains it: sorting the packed values sorts the keys
+// (equal keys lie in the same leaf), and the sort kernel then reads the containing leaf instead of
+// searching for it.
+constexpr int PACK_BITS = 21;  // leaf indices below 2^21 (meshes of this path hold at most 2^20)
 template <int DIM>
 __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl, int64_t n_ub, KG g,
-                               int D, uint64_t* __restrict__ out, int64_t cap) {
+                               int D, uint64_t* __restrict__ out, int64_t cap, bool packed) {
   pdl_wait_then_release();
   constexpr int LPL = BalLanes<DIM>::value;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -380,7 +386,8 @@ __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restri
   const int64_t n = ctl[CTL_OVER] == 0 ? ctl[CTL_N] : 0;
   uint32_t N[3];
   int dA = 0;
-  const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA) : 0;
+  int64_t jA = 0;
+  const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA, &jA) : 0;
   // every lane of the warp takes part: inclusive prefix of the counts, one atomic per warp
   const int lane = int(threadIdx.x & 31);
   int incl = c;
@@ -400,7 +407,10 @@ __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restri
     const uint64_t span = vol_raw<DIM>(g, l - 1);
     const uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
     for (int ch = 0; ch < (1 << DIM); ++ch, ++q)
-      if (q < cap) out[q] = child_key<DIM>(g, anc, ch);  // past the capacity: counted, not stored
+      if (q < cap) {  // past the capacity: counted, not stored
+        const uint64_t ck = child_key<DIM>(g, anc, ch);
+        out[q] = packed ? (ck << PACK_BITS) | uint64_t(jA) : ck;
+      }
   }
 }
 
@@ -410,7 +420,7 @@ __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restri
 template <int DIM>
 __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, int64_t* __restrict__ ctl,
                                                      int64_t cap, int D, const uint64_t* __restrict__ k, KG g,
-                                                     int32_t* __restrict__ P) {
+                                                     int32_t* __restrict__ P, bool packed) {
   pdl_wait_then_release();
   __shared__ uint64_t sk[SMALL_SORT_MAX];
   __shared__ int32_t wsum[32];
@@ -472,19 +482,37 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
   __syncthreads();  // the sorted octants are in S (global writes of this block are visible now)
   // per thread 4 consecutive octants r = 4t .. 4t+3: kept(r) - first(r), with first(r) when the
   // containing leaf of r differs from that of r - 1
+  // (packed: the containing leaf is the value's low bits, the key its high bits; the sorted keys
+  // are written back unpacked once every thread has read its neighbours)
+  const uint64_t lmask = (1ull << PACK_BITS) - 1;
+  auto leaf_of = [&](int r) -> int64_t {
+    return packed ? int64_t(S[r] & lmask) : upper_bound_dev(k, n, S[r]) - 1;
+  };
+  auto keep_of = [&](int r) -> bool {
+    if (!packed) return lin_keep<DIM>(S, nS, g, r);
+    if (r + 1 >= nS) return true;
+    const uint64_t a = S[r] >> PACK_BITS, b = S[r + 1] >> PACK_BITS;
+    return !(a == b || is_ancestor<DIM>(g, a, b));
+  };
   int v[4], sum = 0;
   int64_t prev_leaf = -1;
-  if (4 * t < nS && 4 * t > 0) prev_leaf = upper_bound_dev(k, n, S[4 * t - 1]) - 1;
+  if (4 * t < nS && 4 * t > 0) prev_leaf = leaf_of(4 * t - 1);
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int r = 4 * t + q;
     v[q] = 0;
     if (r < nS) {
-      const int64_t leaf = upper_bound_dev(k, n, S[r]) - 1;
-      v[q] = int(lin_keep<DIM>(S, nS, g, r)) - int(leaf != prev_leaf);
+      const int64_t leaf = leaf_of(r);
+      v[q] = int(keep_of(r)) - int(leaf != prev_leaf);
       prev_leaf = leaf;
     }
     sum += v[q];
+  }
+  if (packed) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (4 * t + q < nS) S[4 * t + q] >>= PACK_BITS;
   }
   // block-wide exclusive scan of the per-thread sums
   const int lane = t & 31, wid = t >> 5;
@@ -971,16 +999,18 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
   for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
     Scratch S(&A);
     const int64_t nb = *n_ub;
+    // key bits and the containing leaf's index fit one 64-bit value
+    const bool packed = dim * g.Dmax + g.mb + PACK_BITS <= 64 && nb < (int64_t(1) << PACK_BITS);
     int32_t* P = S.get<int32_t>(cap + 1);
     if (!P || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap))) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
     DIM_DISPATCH(dim, (launch_dependent(k_bal_gen_fast<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g,
-                                        D, gen.p, cap)));
+                                        D, gen.p, cap, packed)));
     ++launch_counter();
     DIM_DISPATCH(dim, (launch_dependent(k_sort_annot<D_>, 1, 1024, s, gen.p, d_ctl, cap, D,
-                                        static_cast<const uint64_t*>(keys.p), g, P)));
+                                        static_cast<const uint64_t*>(keys.p), g, P, packed)));
     ++launch_counter();
     DIM_DISPATCH(dim, (launch_dependent(k_merge_fast<D_>, nblk(nb), TB, s, static_cast<const uint64_t*>(keys.p),
                                         static_cast<const int64_t*>(d_ctl), nb, static_cast<const uint64_t*>(gen.p),

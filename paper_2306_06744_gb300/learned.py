@@ -106,7 +106,8 @@ def accuracy(params, X, y):
 
 
 def deploy_run(cfg: dict, steps: int, every: int, params=None) -> dict:
-    """Runs `steps` steps adapting every `every` steps; wall time of steps and adaptations."""
+    """Runs `steps` steps adapting every `every` steps (0: never, the initial mesh throughout);
+    wall time of steps and adaptations, the final and the mean leaf count."""
     import time
 
     import torch
@@ -115,21 +116,25 @@ def deploy_run(cfg: dict, steps: int, every: int, params=None) -> dict:
         m.set_learned_indicator(params)
     ts = ta = 0.0
     n_adapt = 0
-    for _ in range(steps // every):
+    chunk = every if every > 0 else 30
+    Ms = []
+    for _ in range(steps // chunk):
+        Ms.append(m.M)
         torch.cuda.synchronize()
         a = time.perf_counter()
-        m.step(every)
+        m.step(chunk)
         torch.cuda.synchronize()
         b = time.perf_counter()
-        m.adapt()
+        if every > 0:
+            m.adapt()
+            n_adapt += 1
         torch.cuda.synchronize()
         c = time.perf_counter()
         ts += b - a
         ta += c - b
-        n_adapt += 1
     nm = m.norms()
-    out = dict(l2_rho=nm["l2_rho"], t=nm["t"], M_final=m.M, steps_s=ts, adapt_s=ta, total_s=ts + ta,
-               adaptations=n_adapt, adaptation_pct=100.0 * ta / (ts + ta))
+    out = dict(l2_rho=nm["l2_rho"], t=nm["t"], M_final=m.M, M_mean=float(np.mean(Ms)), steps_s=ts,
+               adapt_s=ta, total_s=ts + ta, adaptations=n_adapt, adaptation_pct=100.0 * ta / (ts + ta))
     m.close()
     torch.cuda.empty_cache()
     return out
@@ -162,6 +167,42 @@ def experiment(steps: int = 120, snapshots: int = 30, log=print) -> dict:
     res["learned_f64_every30"] = deploy_run(dict(cfg4, precision=0, indicator=3), steps, 30, params)
     res["learned_double_word_every30"] = deploy_run(dict(cfg4, precision=4, indicator=3), steps, 30,
                                                     params)
+    return res
+
+
+def experiment_long(steps: int = 990, snapshots: int = 30, log=print) -> dict:
+    """The same training as `experiment`; deployment on the four 3D p=3 tubes for `steps` steps
+    (a multiple of 10 and 30, so every arm ends at the same time; each vortex moves about 20
+    finest cells) in four arms -- plain indicator every 10 and every
+    30 steps, learned indicator every 30, no adaptation -- in FP64 and in the double-word form."""
+    import time
+
+    import torch
+    cfg4 = W.config("vortex3d_p3_multi")
+    cfg3 = dict(W.config("vortex3d_p2_tube"), precision=4,
+                th_refine=cfg4["th_refine"], th_coarsen=cfg4["th_coarsen"])
+    t0 = time.perf_counter()
+    X, y = collect_pairs(cfg3, snapshots=snapshots, horizon=20, every=10)
+    t_collect = time.perf_counter() - t0
+    n = X.shape[0]
+    ntr = int(0.9 * n)
+    t0 = time.perf_counter()
+    params, hist = train(X[:ntr], y[:ntr], epochs=6, batch=4096, lr=2e-3, log=log)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    acc, conf = accuracy(params, X[ntr:], y[ntr:])
+    res = dict(steps=steps, pairs=int(n), collect_s=t_collect, train_s=t_train, loss_history=hist,
+               heldout_accuracy=acc, confusion=conf.tolist())
+    del X, y
+    torch.cuda.empty_cache()
+    for prec, pname in ((0, "f64"), (4, "double_word")):
+        arms = (("plain_every10", 0, 10), ("plain_every30", 0, 30), ("learned_every30", 3, 30),
+                ("no_adaptation", 0, 0))
+        for arm, ind, every in arms:
+            key = "%s_%s" % (arm, pname)
+            res[key] = deploy_run(dict(cfg4, precision=prec, indicator=ind), steps, every,
+                                  params if ind == 3 else None)
+            log("%s: %s" % (key, res[key]))
     return res
 
 
@@ -227,6 +268,13 @@ if __name__ == "__main__":
         n = int(sys.argv[2]) if len(sys.argv) > 2 else 2_000_000
         n_in = int(sys.argv[3]) if len(sys.argv) > 3 else 55
         print(json.dumps(bench_forward(n, n_in)))
+        sys.exit(0)
+    if len(sys.argv) > 1 and sys.argv[1] == "--long":
+        out = experiment_long(int(sys.argv[3]) if len(sys.argv) > 3 else 990)
+        print(json.dumps(out))
+        if len(sys.argv) > 2:
+            with open(sys.argv[2], "w") as fh:
+                json.dump(out, fh, indent=1)
         sys.exit(0)
     out = experiment()
     print(json.dumps(out))

@@ -192,3 +192,63 @@ def test_four_tube_3d_p3_reduced_levels():
     o.adapt(fo)
     assert np.array_equal(g.leaves(), o.leaves())
     assert rel_l2(g.state(), o.state()) < 1e-12
+
+
+def _points_of(cfg, keys, sel):
+    """Coordinates [len(sel)][N][3] of the solution points of the leaves keys[sel] (oracle's GL
+    nodes, x fastest)."""
+    dim, p, Dmax = cfg["dim"], cfg["p"], cfg["Dmax"]
+    n, N = p + 1, (p + 1) ** dim
+    x = O.operators(p)["x"]
+    bx = O.morton_decode(dim, Dmax, keys[sel])
+    h = cfg["L"] / 2.0 ** bx[:, 0]
+    cell = cfg["L"] / 2.0 ** Dmax
+    idx = np.arange(N)
+    X = np.zeros((len(sel), N, 3))
+    for a in range(dim):
+        X[:, :, a] = bx[:, 1 + a, None] * cell + 0.5 * h[:, None] * (x[(idx // n ** a) % n][None, :] + 1.0)
+    return X
+
+
+def test_full_size_four_tube_workload():
+    # the benchmark's configuration at full size (about 3M leaves, p = 3, ~67 GB on the device):
+    # properties that hold at any size, and outputs the oracle computes one by one
+    cfg = _cfg("vortex3d_p3_multi")
+    g = fr.Mesh(cfg)
+    keys = g.leaves().copy()
+    M = len(keys)
+    assert 2_000_000 <= M <= 4_000_000
+    # a complete, sorted, 2:1-balanced linear tree: strictly ascending keys, volumes summing to
+    # the domain, and the balance (checked against the oracle elsewhere) leaves it unchanged
+    assert np.all(keys[1:] > keys[:-1])
+    depth = O.morton_decode(3, cfg["Dmax"], keys[:: max(1, M // 100000)])[:, 0]
+    assert depth.min() >= cfg["Dbase"] and depth.max() <= cfg["Dmax"]
+    d_all = (keys & np.uint64((1 << 4) - 1)).astype(np.int64)  # depth field (4 bits at Dmax 10)
+    assert np.array_equal(d_all[:: max(1, M // 100000)], depth)
+    assert int(np.sum(np.left_shift(np.int64(1), 3 * (cfg["Dmax"] - d_all)))) == 1 << (3 * cfg["Dmax"])
+    assert np.array_equal(fr.tree_balance(3, cfg["Dmax"], keys), keys)
+    # the initial state is the closed form at the points: 2000 sampled leaves against the oracle
+    sel = np.sort((W.random_uniform(2000, 17) * M).astype(np.int64))
+    u = g.state()
+    want = O.exact(cfg, 0.0, _points_of(cfg, keys, sel).reshape(-1, 3)).reshape(len(sel), 64, 5)
+    assert rel_l2(u[sel].transpose(0, 2, 1), want) < 1e-13
+    # one step: the conserved integrals of the periodic box do not move (discrete conservation)
+    i0 = np.array(g.norms()["integral"])
+    g.step(1)
+    i1 = np.array(g.norms()["integral"])
+    assert np.all(np.abs(i1 - i0) <= 1e-12 * np.abs(i0) + 1e-9), (i0, i1)
+    # the split-BF16 tensor-core form on the same mesh and state: one step stays within 1e-6 of FP64
+    gt = fr.Mesh(dict(cfg, precision=3, init_passes=0, indicator=2, dt=g.info()["dt"]))
+    gt.set_state(keys, u)
+    g.set_state(keys, u)
+    g.set_time(0.0)
+    g.step(1)
+    gt.step(1)
+    assert rel_l2(gt.state(), g.state()) < 1e-6
+    gt.close()
+    # freestream preservation on the full mesh
+    q = np.array([1.2, 0.5, -0.3, 0.2, 0.0])
+    q[-1] = 2.5 + 0.5 * (q[1:4] ** 2).sum() / q[0]
+    g.set_state(keys, np.broadcast_to(q[None, :, None], (M, 5, 64)))
+    assert np.abs(g.rhs()).max() < 1e-11
+    g.close()
