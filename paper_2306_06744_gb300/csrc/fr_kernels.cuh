@@ -154,23 +154,39 @@ __device__ __forceinline__ ff cst<ff>(double x) {
   return ff_from_double(x);
 }
 
-// traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1)
+// traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1).
+// Blocks of EPB elements as in the element kernel: the elements' state is staged in shared memory
+// with coalesced loads, then one thread per (element, face, face point) forms all variables.
 template <int DIM, int NP, class T>
-__global__ void k_traces_t(const double* __restrict__ u, int64_t M, const __grid_constant__ OpsT<T> ops,
-                           T* __restrict__ tr) {
+__global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_traces_t(const double* __restrict__ u, int64_t M,
+                                                              const __grid_constant__ OpsT<T> ops,
+                                                              T* __restrict__ tr) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
-  int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= M * S::EF) return;
-  int64_t e = idx / S::EF;
-  int r = int(idx % S::EF);
-  int f = r / (S::NV * S::NF), v = (r / S::NF) % S::NV, q = r % S::NF;
-  const T* lf = (f & 1) ? ops.lp : ops.lm;
-  const double* ue = u + (e * S::NV + v) * S::N;
-  T s = zero_t<T>();
+  constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF, EPB = S::EPB;
+  constexpr int FQ = S::NFC * NF;
+  __shared__ T su[EPB * EU];
+  const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  const int ne = int((M - e0) < EPB ? (M - e0) : EPB);
+  for (int k = threadIdx.x; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(u[e0 * EU + k]);
+  __syncthreads();
+  for (int k = threadIdx.x; k < ne * FQ; k += blockDim.x) {
+    const int le = k / FQ, r = k % FQ;
+    const int f = r / NF, q = r % NF;
+    const T* lf = (f & 1) ? ops.lp : ops.lm;
+    int pts[NP];
 #pragma unroll
-  for (int j = 0; j < NP; ++j) s = fma_t(lf[j], Ar<T>::from_d(ue[line_pt<DIM, NP>(f >> 1, q, j)]), s);
-  tr[idx] = s;
+    for (int j = 0; j < NP; ++j) pts[j] = line_pt<DIM, NP>(f >> 1, q, j);
+    T* to = tr + (e0 + le) * EF + f * NV * NF + q;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const T* ue = su + le * EU + v * N;
+      T s = zero_t<T>();
+#pragma unroll
+      for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[pts[j]], s);
+      to[v * NF] = s;
+    }
+  }
 }
 
 // interface kernel: blocks [0, nb_hang) do hanging faces (one block slice per coarse face: Rusanov
@@ -558,9 +574,11 @@ int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps&
                        cudaStream_t s, Err* err) {
   if (M <= 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
-  int64_t Tn = M * 2 * dim * (dim + 2) * ipow_k(p + 1, dim - 1);
-  unsigned nb = unsigned((Tn + 127) / 128);
-  FR_NP_DISPATCH(dim, p, (launch_dependent(k_traces_t<DD, NN, T>, nb, 128, s, u, M, ops, static_cast<T*>(tr))));
+  FR_NP_DISPATCH(dim, p, ({
+                   using SS = Sz<DD, NN>;
+                   const unsigned nb = unsigned((M + SS::EPB - 1) / SS::EPB);
+                   launch_dependent(k_traces_t<DD, NN, T>, nb, SS::BT, s, u, M, ops, static_cast<T*>(tr));
+                 }));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -257,88 +257,117 @@ __global__ void k_indicator(const uint64_t* __restrict__ keys, int64_t M, KG g, 
 }
 
 // Solution transfer (Sec. 4.2): copy; interpolation of the old (ancestor) polynomial at the new
-// points, with the Lagrange weights evaluated in the kernel; L2 projection of 2^dim fused
-// children with the tensor-product operators P (exact-quadrature mass and cross-mass matrices).
-// One thread per new point, 128 per block.  Without a mapping (src null) the block first maps
-// its own new leaves (one lower bound each, into shared memory), so the adaptation needs no
-// separate mapping kernel.
-constexpr int XFER_T = 128;
+// points; L2 projection of 2^dim fused children onto the parent.  Both non-trivial cases are
+// tensor products of 1D operators and are applied axis by axis (sum factorisation: DIM
+// contractions of length n per output value instead of one of length N): for refinement the
+// 1D Lagrange weights of the ancestor at the new points, for fusion the 1D projection operators
+// P (exact-quadrature mass and cross-mass matrices), one child after the other.
+// Blocks of EPB whole elements, one thread per point (as the element kernel).  Without a mapping
+// (src null) each element's first thread maps its new leaf (one lower bound) into shared memory,
+// so the adaptation needs no separate mapping kernel.
 template <int DIM, int NP>
-__global__ void __launch_bounds__(XFER_T) k_transfer(KG g, const uint64_t* __restrict__ old_keys, int64_t n_old,
-                                                     const uint64_t* __restrict__ new_keys,
-                                                     const int32_t* __restrict__ src, const int8_t* __restrict__ tag,
-                                                     int32_t* bad, int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
-                                                     const __grid_constant__ DevOps ops, const double* __restrict__ uo,
-                                                     double* __restrict__ un) {
+__global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_transfer(KG g, const uint64_t* __restrict__ old_keys,
+                                                              int64_t n_old, const uint64_t* __restrict__ new_keys,
+                                                              const int32_t* __restrict__ src,
+                                                              const int8_t* __restrict__ tag, int32_t* bad,
+                                                              int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
+                                                              const __grid_constant__ DevOps ops,
+                                                              const double* __restrict__ uo,
+                                                              double* __restrict__ un) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
-  constexpr int LMAX = XFER_T / S::N + 2;  // new leaves a block's points can touch
-  __shared__ int32_t s_src[LMAX];
-  __shared__ int8_t s_tag[LMAX];
-  const int64_t idx0 = int64_t(blockIdx.x) * XFER_T;
+  constexpr int N = S::N, NV = S::NV, EU = S::EU, EPB = S::EPB;
+  __shared__ double sa[EPB][EU], sb[EPB][EU];
+  __shared__ double sw[EPB][DIM][NP][NP];  // refinement: 1D weights w[a][i][m] = l_m(xi_a(i))
+  __shared__ int32_t s_src[EPB];
+  __shared__ int8_t s_tag[EPB];
+  __shared__ int s_rounds;
   const int64_t Mn = (d_Mn && *d_Mn < Mn_ub) ? *d_Mn : Mn_ub;
-  const int64_t j0 = idx0 / S::N;
-  if (!src) {
-    const int t = threadIdx.x;
-    const int64_t jt = j0 + t;
-    if (t < LMAX && jt < Mn && jt * S::N < idx0 + XFER_T)
-      map_leaf<DIM>(old_keys, n_old, new_keys[jt], g, &s_src[t], &s_tag[t], bad);
-    __syncthreads();
+  const int64_t j0 = int64_t(blockIdx.x) * EPB;
+  const int le = threadIdx.x / N, i = threadIdx.x % N;
+  const int64_t j = j0 + le;
+  const bool act = le < EPB && j < Mn;
+  if (threadIdx.x == 0) s_rounds = 0;
+  if (act && i == 0) {
+    if (src) {
+      s_src[le] = src[j];
+      s_tag[le] = tag[j];
+    } else {
+      map_leaf<DIM>(old_keys, n_old, new_keys[j], g, &s_src[le], &s_tag[le], bad);
+    }
   }
-  const int64_t idx = idx0 + threadIdx.x;
-  if (idx >= Mn * S::N) return;
-  const int64_t j = idx / S::N;
-  const int i = int(idx % S::N);
-  const int64_t sidx = src ? src[j] : s_src[j - j0];
-  const int tg = src ? tag[j] : s_tag[j - j0];
-  int ii[3] = {i % NP, (i / NP) % NP, DIM == 3 ? i / (NP * NP) : 0};
-  if (tg == 0) {
+  __syncthreads();
+  const int64_t sidx = act ? s_src[le] : 0;
+  const int tg = act ? s_tag[le] : 0;
+  const int ii[3] = {i % NP, (i / NP) % NP, DIM == 3 ? i / (NP * NP) : 0};
+  if (act && tg == 0) {
 #pragma unroll
-    for (int v = 0; v < S::NV; ++v) un[(j * S::NV + v) * S::N + i] = uo[(sidx * S::NV + v) * S::N + i];
-  } else if (tg == 1) {
-    uint64_t kA = old_keys[sidx], kK = new_keys[j];
+    for (int v = 0; v < NV; ++v) un[(j * NV + v) * N + i] = uo[(sidx * NV + v) * N + i];
+  }
+  // rounds of the contraction: 1 for a refined element, 2^dim (one per child) for a fused one
+  if (act && i == 0 && tg != 0) atomicMax(&s_rounds, tg == 1 ? 1 : (1 << DIM));
+  if (act && tg == 1) {
+    // 1D Lagrange weights of the ancestor at the new element's points along each axis
+    const uint64_t kA = old_keys[sidx], kK = new_keys[j];
     uint32_t xa[3] = {0, 0, 0}, xk[3] = {0, 0, 0};
     deinterleave<DIM>(g.raw(kA), xa);
     deinterleave<DIM>(g.raw(kK), xk);
-    double wA = double(g.width(g.depth(kA))), wK = double(g.width(g.depth(kK)));
-    double lw[DIM][NP];
+    const double wA = double(g.width(g.depth(kA))), wK = double(g.width(g.depth(kK)));
+    for (int w = i; w < DIM * NP * NP; w += N) {
+      const int a = w / (NP * NP), ia = (w / NP) % NP, m = w % NP;
+      const double xi = -1.0 + 2.0 * (double(xk[a] - xa[a]) + 0.5 * (ops.x[ia] + 1.0) * wK) / wA;
+      double pr = 1.0;
+#pragma unroll
+      for (int k = 0; k < NP; ++k)
+        if (k != m) pr *= (xi - ops.x[k]) / (ops.x[m] - ops.x[k]);
+      sw[le][a][ia][m] = pr;
+    }
+  }
+  __syncthreads();
+  const int rounds = s_rounds;
+  double acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+  const bool work = act && tg != 0;
+  for (int r = 0; r < rounds; ++r) {
+    // the round's source: the ancestor (refinement) or child r (fusion)
+    const bool live = work && (tg == 2 || r == 0);
+    if (live) {
+      const int64_t se = tg == 2 ? sidx + r : sidx;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sa[le][v * N + i] = uo[(se * NV + v) * N + i];
+    }
+    __syncthreads();
+    // axis by axis: along x from sa into sb, along y from sb into sa, along z from sa into sb
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-      double xi = -1.0 + 2.0 * (double(xk[a] - xa[a]) + 0.5 * (ops.x[ii[a]] + 1.0) * wK) / wA;
+      double* in = (a & 1) ? sb[le] : sa[le];
+      double* out = (a & 1) ? sa[le] : sb[le];
+      if (live) {
+        const int h = (r >> a) & 1;
+        const int stride = a == 0 ? 1 : (a == 1 ? NP : NP * NP);
+        const int base = i - ii[a] * stride;  // the point with index 0 along axis a
 #pragma unroll
-      for (int m = 0; m < NP; ++m) {
-        double pr = 1.0;
+        for (int v = 0; v < NV; ++v) {
+          double t = 0.0;
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-          if (k != m) pr *= (xi - ops.x[k]) / (ops.x[m] - ops.x[k]);
-        lw[a][m] = pr;
-      }
-    }
-    for (int v = 0; v < S::NV; ++v) {
-      const double* ua = uo + (sidx * S::NV + v) * S::N;
-      double acc = 0.0;
-      for (int q = 0; q < S::N; ++q) {
-        double wq = lw[0][q % NP] * lw[1][(q / NP) % NP];
-        if (DIM == 3) wq *= lw[DIM - 1][q / (NP * NP)];
-        acc += wq * ua[q];
-      }
-      un[(j * S::NV + v) * S::N + i] = acc;
-    }
-  } else {
-    for (int v = 0; v < S::NV; ++v) {
-      double acc = 0.0;
-      for (int c = 0; c < (1 << DIM); ++c) {
-        const double* uc = uo + ((sidx + c) * S::NV + v) * S::N;
-        int h0 = c & 1, h1 = (c >> 1) & 1, h2 = (c >> 2) & 1;
-        for (int q = 0; q < S::N; ++q) {
-          int q0 = q % NP, q1 = (q / NP) % NP, q2 = DIM == 3 ? q / (NP * NP) : 0;
-          double wq = ops.P[h0][ii[0]][q0] * ops.P[h1][ii[1]][q1];
-          if (DIM == 3) wq *= ops.P[h2][ii[2]][q2];
-          acc += wq * uc[q];
+          for (int m = 0; m < NP; ++m) {
+            const double wgt = tg == 1 ? sw[le][a][ii[a]][m] : ops.P[h][ii[a]][m];
+            t = fma(wgt, in[v * N + base + m * stride], t);
+          }
+          if (a == DIM - 1)
+            acc[v] += t;
+          else
+            out[v * N + i] = t;
         }
       }
-      un[(j * S::NV + v) * S::N + i] = acc;
+      if (a < DIM - 1) __syncthreads();
     }
+    __syncthreads();  // the next round overwrites sa
+  }
+  if (work) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) un[(j * NV + v) * N + i] = acc[v];
   }
 }
 
@@ -514,9 +543,11 @@ int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64
                     const int32_t* src, const int8_t* tag, int32_t* bad, int64_t M_new, const int64_t* d_M_new,
                     const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err) {
   if (M_new <= 0) return 0;
-  int64_t T = M_new * ipow(p + 1, dim);
-  FR_DISPATCH(dim, p, (launch_dependent(k_transfer<DD, NN>, nb_of(T, XFER_T), XFER_T, s, g, old_keys, n_old, new_keys,
-                                        src, tag, bad, M_new, d_M_new, ops, u_old, u_new)));
+  FR_DISPATCH(dim, p, ({
+                using SS = Sz<DD, NN>;
+                launch_dependent(k_transfer<DD, NN>, unsigned((M_new + SS::EPB - 1) / SS::EPB), SS::BT, s, g,
+                                 old_keys, n_old, new_keys, src, tag, bad, M_new, d_M_new, ops, u_old, u_new);
+              }));
   FR_LAUNCH_CHECK(err);
   return 0;
 }

@@ -368,11 +368,9 @@ def paper_uniform_cfg(p, D, dt):
 
 
 # coarsest row of the table; the time steps are larger than the paper's 0.001, with time errors
-# far below the spatial ones (p = 1: dt = 0.004, 0.008 and 0.0125 agree to 0.02%).  p = 2 and 3
-# take minutes on the oracle (about 90 s and 230 s here): FR_SLOW_PINS=1 runs them.
-@pytest.mark.parametrize("p,dt,tol", [(1, 0.0125, 0.02),
-                                      pytest.param(2, 0.00625, 0.02, marks=pytest.mark.skipif(
-                                          not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS")),
+# far below the spatial ones (p = 1: dt = 0.004, 0.008 and 0.0125 agree to 0.02%).  p = 2 takes
+# about 90 s on the oracle and runs by default; p = 3 (about 230 s) with FR_SLOW_PINS=1.
+@pytest.mark.parametrize("p,dt,tol", [(1, 0.0125, 0.02), (2, 0.00625, 0.02),
                                       pytest.param(3, 0.005, 0.02, marks=pytest.mark.skipif(
                                           not os.environ.get("FR_SLOW_PINS"), reason="FR_SLOW_PINS"))])
 def test_paper_uniform_l2_error(p, dt, tol):
