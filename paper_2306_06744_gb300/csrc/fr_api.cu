@@ -198,9 +198,11 @@ int ensure_state(fr_mesh* m, int64_t M) {
   return 0;
 }
 
-int refresh_traces(fr_mesh* m) {
+// traces of the current state (mask: only of the elements with a non-zero entry, the others
+// already hold theirs)
+int refresh_traces(fr_mesh* m, const int8_t* mask = nullptr) {
   m->traces_ok = false;
-  FR_TRY(launch_traces(m->cfg.precision, m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err));
+  FR_TRY(launch_traces(m->cfg.precision, m->dim, m->p, m->u.p, m->M, m->ops, m->trace.p, m->stream, &m->err, mask));
   m->traces_ok = true;
   return 0;
 }
@@ -375,8 +377,12 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<uint64_t> nk;
   Buf<double> nu;
   Buf<int32_t> src, hcon;
-  Buf<int8_t> tag;
+  Buf<int8_t> tag, retr;
+  Buf<double> ntr;
   bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
+  // the traces of unchanged elements are carried over by the transfer (when the current ones are
+  // valid); only refined and fused elements get theirs computed afterwards
+  const bool carry = transfer && m->traces_ok;
   int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
@@ -392,9 +398,15 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       }
       T.mark(1);
       if (!r) r = nu.ensure(m->A, size_t(nb) * m->EU);
+      TraceCopy tc{};
+      if (!r && carry) {
+        r = ntr.ensure(m->A, size_t(nb) * m->EF);
+        if (!r) r = retr.ensure(m->A, size_t(nb));
+        tc = TraceCopy{m->trace.p, ntr.p, retr.p, m->EF * trace_elem_bytes(m->cfg.precision)};
+      }
       if (!r)
         r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, fast ? nullptr : src.p, fast ? nullptr : tag.p,
-                            bad + 1, nb, d_n, m->ops, m->u.p, nu.p, s, err);
+                            bad + 1, nb, d_n, m->ops, m->u.p, nu.p, tc, s, err);
     } else {
       T.mark(1);
     }
@@ -441,7 +453,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     // that is released and not replaced here is grown again by ready_buffers)
     m->traces_ok = false;
     rc = m->w.ensure(m->A, size_t(M1) * m->EU);
-    if (!rc) rc = m->trace.ensure(m->A, size_t(M1) * m->EF);
+    if (!rc && !carry) rc = m->trace.ensure(m->A, size_t(M1) * m->EF);
     if (!rc) rc = m->fcomm.ensure(m->A, size_t(M1) * m->EF);
     if (!rc) rc = m->flags.ensure(m->A, size_t(M1));
     if (!rc && !transfer) rc = m->u.ensure(m->A, size_t(M1) * m->EU);
@@ -452,6 +464,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     nk.release(m->A);
     nu.release(m->A);
     hcon.release(m->A);
+    ntr.release(m->A);
+    retr.release(m->A);
     if (conn_dirty) {
       Err keep = *err;
       rebuild_conn(m);
@@ -468,12 +482,19 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     m->u = nu;
     ou.release(m->A);
   }
+  if (carry) {
+    Buf<double> ot = m->trace;  // the carried traces become the mesh's
+    m->trace = ntr;
+    ntr = Buf<double>{};
+    ot.release(m->A);
+  }
   m->traces_ok = false;
   m->flags_fresh = false;
   rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
   hcon.release(m->A);
+  if (!rc && transfer) rc = refresh_traces(m, carry ? retr.p : nullptr);
+  retr.release(m->A);
   FR_TRY(rc);
-  if (transfer) FR_TRY(refresh_traces(m));
   T.mark(3);
   if (st) {
     st->M_old = M0;

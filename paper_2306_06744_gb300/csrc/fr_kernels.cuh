@@ -160,18 +160,23 @@ __device__ __forceinline__ ff cst<ff>(double x) {
 template <int DIM, int NP, class T>
 __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_traces_t(const double* __restrict__ u, int64_t M,
                                                               const __grid_constant__ OpsT<T> ops,
-                                                              T* __restrict__ tr) {
+                                                              T* __restrict__ tr, const int8_t* __restrict__ mask) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF, EPB = S::EPB;
   constexpr int FQ = S::NFC * NF;
   __shared__ T su[EPB * EU];
+  __shared__ int8_t need[EPB];
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
   const int ne = int((M - e0) < EPB ? (M - e0) : EPB);
-  for (int k = threadIdx.x; k < ne * EU; k += blockDim.x) su[k] = Ar<T>::from_d(u[e0 * EU + k]);
+  if (threadIdx.x < ne) need[threadIdx.x] = mask ? mask[e0 + threadIdx.x] : 1;
+  __syncthreads();
+  for (int k = threadIdx.x; k < ne * EU; k += blockDim.x)
+    if (need[k / EU]) su[k] = Ar<T>::from_d(u[e0 * EU + k]);
   __syncthreads();
   for (int k = threadIdx.x; k < ne * FQ; k += blockDim.x) {
     const int le = k / FQ, r = k % FQ;
+    if (!need[le]) continue;
     const int f = r / NF, q = r % NF;
     const T* lf = (f & 1) ? ops.lp : ops.lm;
     int pts[NP];
@@ -571,13 +576,13 @@ inline int ipow_k(int b, int e) {
 
 template <class T>
 int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps& o, void* tr,
-                       cudaStream_t s, Err* err) {
+                       const int8_t* mask, cudaStream_t s, Err* err) {
   if (M <= 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    const unsigned nb = unsigned((M + SS::EPB - 1) / SS::EPB);
-                   launch_dependent(k_traces_t<DD, NN, T>, nb, SS::BT, s, u, M, ops, static_cast<T*>(tr));
+                   launch_dependent(k_traces_t<DD, NN, T>, nb, SS::BT, s, u, M, ops, static_cast<T*>(tr), mask);
                  }));
   FR_LAUNCH_CHECK(err);
   return 0;

@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_transfer(KG g, const uint64
                                                               int64_t Mn_ub, const int64_t* __restrict__ d_Mn,
                                                               const __grid_constant__ DevOps ops,
                                                               const double* __restrict__ uo,
-                                                              double* __restrict__ un) {
+                                                              double* __restrict__ un, const TraceCopy tc) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   constexpr int N = S::N, NV = S::NV, EU = S::EU, EPB = S::EPB;
@@ -303,7 +303,15 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_transfer(KG g, const uint64
   if (act && tg == 0) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) un[(j * NV + v) * N + i] = uo[(sidx * NV + v) * N + i];
+    // an unchanged element keeps its traces: copied as 8-byte words
+    if (tc.dst) {
+      const int w = tc.bytes >> 3;
+      const uint64_t* a = static_cast<const uint64_t*>(tc.src) + sidx * w;
+      uint64_t* b = static_cast<uint64_t*>(tc.dst) + j * w;
+      for (int k = i; k < w; k += N) b[k] = a[k];
+    }
   }
+  if (act && i == 0 && tc.retrace) tc.retrace[j] = int8_t(tg != 0);
   // rounds of the contraction: 1 for a refined element, 2^dim (one per child) for a fused one
   if (act && i == 0 && tg != 0) atomicMax(&s_rounds, tg == 1 ? 1 : (1 << DIM));
   if (act && tg == 1) {
@@ -508,10 +516,10 @@ int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, d
 }
 
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
-                  cudaStream_t s, Err* err) {
-  if (prec >= 1 && prec <= 3) return launch_traces_f32(dim, p, u, M, ops, tr, s, err);
-  if (prec == 4) return launch_traces_ff(dim, p, u, M, ops, tr, s, err);
-  return launch_traces_f64(dim, p, u, M, ops, tr, s, err);
+                  cudaStream_t s, Err* err, const int8_t* mask) {
+  if (prec >= 1 && prec <= 3) return launch_traces_f32(dim, p, u, M, ops, tr, mask, s, err);
+  if (prec == 4) return launch_traces_ff(dim, p, u, M, ops, tr, mask, s, err);
+  return launch_traces_f64(dim, p, u, M, ops, tr, mask, s, err);
 }
 
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {
@@ -541,12 +549,13 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
 
 int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64_t n_old, const uint64_t* new_keys,
                     const int32_t* src, const int8_t* tag, int32_t* bad, int64_t M_new, const int64_t* d_M_new,
-                    const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err) {
+                    const DevOps& ops, const double* u_old, double* u_new, const TraceCopy& tc, cudaStream_t s,
+                    Err* err) {
   if (M_new <= 0) return 0;
   FR_DISPATCH(dim, p, ({
                 using SS = Sz<DD, NN>;
                 launch_dependent(k_transfer<DD, NN>, unsigned((M_new + SS::EPB - 1) / SS::EPB), SS::BT, s, g,
-                                 old_keys, n_old, new_keys, src, tag, bad, M_new, d_M_new, ops, u_old, u_new);
+                                 old_keys, n_old, new_keys, src, tag, bad, M_new, d_M_new, ops, u_old, u_new, tc);
               }));
   FR_LAUNCH_CHECK(err);
   return 0;

@@ -35,16 +35,19 @@ struct Mesh;  // defined in fr_api.cu
 int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
                  const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err);
 // prec: 0 FP64, 1 FP32 with FP64 Runge-Kutta combination, 2 TF32 and 3 bf16x3 tensor-core
-// derivative (otherwise as 1; 3D p = 3), 4 double-word (two floats)
+// derivative (otherwise as 1; 3D p = 3), 4 double-word (two floats).  mask (nullable): traces only
+// of the elements with a non-zero entry
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
-                  cudaStream_t s, Err* err);
+                  cudaStream_t s, Err* err, const int8_t* mask = nullptr);
+// bytes of one element's traces in the arithmetic type of `prec`
+inline int trace_elem_bytes(int prec) { return (prec >= 1 && prec <= 3) ? 4 : 8; }
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
 int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s,
                  Err* err);
 // per-precision instantiations (fr_prec_f64.cu, fr_prec_f32.cu, fr_prec_ff.cu)
 #define FR_DECLARE_PREC(sfx)                                                                    \
   int launch_traces_##sfx(int dim, int p, const double* u, int64_t M, const DevOps& ops,        \
-                          void* tr, cudaStream_t s, Err* err);                                  \
+                          void* tr, const int8_t* mask, cudaStream_t s, Err* err);              \
   int launch_faces_##sfx(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s,         \
                          Err* err);                                                             \
   int launch_stage_##sfx(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, \
@@ -59,11 +62,21 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
                      const uint64_t* keys, int64_t M, const KG& g, const DevProblem& P,
                      const DevOps& ops, const double* u, int8_t* flags, double* eta,
                      cudaStream_t s, Err* err);
+// Traces carried over by the transfer (all null: none): an unchanged element's `bytes` of traces
+// are copied from src (old elements) to dst (new elements), and retrace[j] says whether new
+// element j needs its traces computed.
+struct TraceCopy {
+  const void* src;
+  void* dst;
+  int8_t* retrace;
+  int bytes;
+};
 // d_M_new (nullable): device count of new leaves, M_new then an upper bound.  src/tag: the
 // old->new mapping, or null: the kernel maps the new leaves itself (mapping failures set *bad)
 int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64_t n_old, const uint64_t* new_keys,
                     const int32_t* src, const int8_t* tag, int32_t* bad, int64_t M_new, const int64_t* d_M_new,
-                    const DevOps& ops, const double* u_old, double* u_new, cudaStream_t s, Err* err);
+                    const DevOps& ops, const double* u_old, double* u_new, const TraceCopy& tc, cudaStream_t s,
+                    Err* err);
 // norms: out[0] = sum w|J|(rho_ex-rho)^2, out[1..nv] integrals, out[nv+1] min rho, out[nv+2] min p
 int launch_norms(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, double t,
                  const DevProblem& P, const DevOps& ops, const double* u, double* d_partial,
