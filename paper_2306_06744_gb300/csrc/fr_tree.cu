@@ -552,28 +552,42 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
   }
 }
 
+// the sorted octants (at most SMALL_SORT_MAX) are staged in shared memory: every leaf searches them
+__device__ __forceinline__ int lower_bound_sh(const uint64_t* a, int n, uint64_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
 template <int DIM>
 __global__ void k_merge_fast(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl, int64_t n_ub,
                              const uint64_t* __restrict__ S, const int32_t* __restrict__ P, KG g,
                              uint64_t* __restrict__ out) {
   pdl_wait_then_release();
+  __shared__ uint64_t sS[SMALL_SORT_MAX];
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_ub || i >= ctl[CTL_NPREV]) return;
-  const int64_t nS = ctl[CTL_GS];
+  const int64_t n = ctl[CTL_NPREV];
+  const int nS = int(ctl[CTL_GS]);  // at most SMALL_SORT_MAX (the sort kernel's capacity check)
+  if (int64_t(blockIdx.x) * blockDim.x >= n) return;  // the whole block is past the leaves
+  for (int r = threadIdx.x; r < nS; r += blockDim.x) sS[r] = S[r];
+  __syncthreads();
+  if (i >= n_ub || i >= n) return;
   const uint64_t key = k[i];
   if (nS == 0) {
     out[i] = key;
     return;
   }
-  const int64_t lo = lower_bound_dev(S, nS, key);
-  const int64_t hi = lower_bound_dev(S, nS, key_end<DIM>(g, key));
+  const int64_t lo = lower_bound_sh(sS, nS, key);
+  const int64_t hi = lower_bound_sh(sS, nS, key_end<DIM>(g, key));
   int64_t o = i + P[lo];
   if (hi == lo) {
     out[o] = key;
     return;
   }
   for (int64_t r = lo; r < hi; ++r)
-    if (lin_keep<DIM>(S, nS, g, r)) out[o++] = S[r];
+    if (lin_keep<DIM>(sS, nS, g, r)) out[o++] = sS[r];
 }
 
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
