@@ -465,14 +465,19 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
     }
     const double cs = sh2[le];
     if constexpr (!std::is_same<T, ff>::value) {
-      // FP64 combination (native FP64 and the mixed FP32 form); b = 1 (first stage) skips the
-      // product, which is exact there
+      // FP64 combination (native FP64 and the mixed FP32 form).  The first stage (a = 0, b = 1)
+      // is one FMA per value; the branch is uniform over the grid (kernel arguments), so the
+      // other stages do not pay for it
+      if (A.a == 0.0 && A.b == 1.0) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const double us = usr[v];
-        double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? us : A.b * us);
-        if (A.a != 0.0) o = fma(A.a, unr[v], o);
-        outv[v] = o;
+        for (int v = 0; v < NV; ++v) outv[v] = fma(cs, Ar<T>::to_d(R[v]), usr[v]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? usr[v] : A.b * usr[v]);
+          if (A.a != 0.0) o = fma(A.a, unr[v], o);
+          outv[v] = o;
+        }
       }
     } else {
       // double-word combination
