@@ -353,6 +353,14 @@ struct RkT<ff> {
   using type = ff;
 };
 
+// Resident blocks the element kernel is compiled for: the FP32 form is bound by memory latency
+// and wants every block shared memory allows (the register budget is set to fit them); the others
+// keep the compiler's choice.
+template <class T>
+struct StageMinBlocks {
+  static constexpr int value = std::is_same<T, float>::value ? 12 : 1;
+};
+
 // element stage: R = -sum_a (2/h) [ sum_j Dt_ij f_j + gL_i F(-1) + gR_i F(+1) ] along each axis
 // (corrected-flux derivative of Sec. 2.1 with the correction folded into Dt; the interface kernel
 // stores 2F and the slopes carry the 1/2), then out = a*un + b*us + c*R (Eq. rk3), and
@@ -360,7 +368,7 @@ struct RkT<ff> {
 // sum_j Dt_ij f_j, all before the wait on the interface kernel; then its common fluxes ->
 // correction terms, Runge-Kutta combination, traces.
 template <int DIM, int NP, class T>
-__global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
+__global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_stage_t(StageArgs A, const __grid_constant__ OpsT<T> ops) {
   using S = Sz<DIM, NP>;
   using RT = typename RkT<T>::type;
   constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF;
@@ -378,18 +386,16 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
   // the stage's input state, the state at the start of the step and the keys come from earlier
   // launches than the interface kernel this one depends on, so they are read, and the pointwise
   // fluxes formed from them, while that kernel drains; the common fluxes are read after it.  Each
-  // thread loads its own point; the FP64 values of u_s (FP32 form) and u^n stay in registers for
-  // the Runge-Kutta combination.
+  // thread loads its own point; its u^n stays in registers for the Runge-Kutta combination.
   const int le = tid / N, i = tid % N;
   const bool act = le < ne;
-  double usr[NV], unr[NV];
+  double unr[NV];
   if (act) {
     const int64_t b0 = (e0 + le) * EU + i;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      usr[v] = A.us[b0 + v * N];
       unr[v] = A.a != 0.0 ? A.un[b0 + v * N] : 0.0;
-      su[le * EU + v * N + i] = Ar<T>::from_d(usr[v]);
+      su[le * EU + v * N + i] = Ar<T>::from_d(A.us[b0 + v * N]);
     }
   }
   // c * (-2/h): 2^depth * (2/L) is exact, so this equals the rounded -2^(depth+1)/L times c
@@ -464,6 +470,13 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_stage_t(StageArgs A, const 
       for (int v = 0; v < NV; ++v) R[v] = fma_t(ops.gLh[ia], Fm[v * NF], fma_t(ops.gRh[ia], Fp[v * NF], R[v]));
     }
     const double cs = sh2[le];
+    // u_s in FP64: the staged copy where it is exact (FP64 form), else the state in memory (an
+    // L2 hit: this block read it at its start); kept out of registers to hold the occupancy
+    double usr[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      usr[v] = std::is_same<T, double>::value ? Ar<T>::to_d(su[le * EU + v * N + i])
+                                              : A.us[(e0 + le) * EU + v * N + i];
     if constexpr (!std::is_same<T, ff>::value) {
       // FP64 combination (native FP64 and the mixed FP32 form).  The first stage (a = 0, b = 1)
       // is one FMA per value; the branch is uniform over the grid (kernel arguments), so the
