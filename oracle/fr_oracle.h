@@ -18,6 +18,12 @@
  *           lower axis least significant, Sec. 3.3; 0 for ftype 2; -1 for conforming).  For
  *           ftype 2, nbr is the slot-0 contributor.
  *
+ * Pins: every function is checked by the CPU test suite against facts that do not come from this
+ * code (brute force on small trees, closed forms, invariants, textbook operators, the paper's
+ * printed values).  Parity unpinned: the refine/coarsen thresholds of the density-gradient
+ * indicator and the CFL time-step rule are choices of this build, not of the paper (the
+ * indicator value eta itself is pinned).
+ *
  * Return codes: 0 success, negative on error (message via oracle_last_error()).
  */
 #ifndef FR_ORACLE_H
