@@ -114,14 +114,31 @@ int check_cfg(const fr_config* c, Err* err) {
 // Issues the connectivity and face lists of `keys` into the mesh's tables: the leaf count is
 // *d_n on the device (at most n_ub) or exactly n_ub (d_n null).  The packed face-list counts go
 // to *d_faces and a 2:1 violation to bad[0]; `hcon` receives the per-hanging-face contributors.
+// append: *d_faces holds zero and the connectivity kernel appends the faces to the lists itself
+// (one launch; the lists' order then varies from run to run, the fluxes do not); otherwise the
+// lists are written in leaf order after a scan of the per-leaf counts.
 static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int64_t* d_n, int64_t* d_faces,
-                      int32_t* bad, Buf<int32_t>& hcon) {
+                      int32_t* bad, Buf<int32_t>& hcon, bool append = false) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
   const int64_t S = n_ub * m->nfc;
   FR_TRY(m->nbr.ensure(m->A, S));
   FR_TRY(m->ftype.ensure(m->A, S));
   FR_TRY(m->slot.ensure(m->A, S));
+  // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
+  // bound so the writes need no synchronisation
+  if (append) {
+    FR_TRY(m->conf.ensure(m->A, size_t(n_ub) * m->dim));
+    FR_TRY(m->hang.ensure(m->A, size_t(n_ub) * m->nfc));
+    FR_TRY(hcon.ensure(m->A, size_t(n_ub) * m->nfc * 4));
+    FaceLists L;
+    L.conf = m->conf.p;
+    L.hang = m->hang.p;
+    L.hcon = hcon.p;
+    L.count = reinterpret_cast<unsigned long long*>(d_faces);
+    return tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, nullptr, bad, s, err,
+                     nullptr, L);
+  }
   FR_TRY(m->contrib.ensure(m->A, S * 4));
   Scratch Sc(&m->A);
   int64_t* cnt = Sc.get<int64_t>(n_ub);
@@ -131,8 +148,6 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
   FR_TRY(tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, m->contrib.p, bad, s, err, cnt));
   Offs O;
   FR_TRY(scan_counts64_local(cnt, off, n_ub, d_faces, Sc, s, err, &O));
-  // the lists hold at most dim conforming and 2*dim hanging entries per element: allocate that
-  // bound so the writes need no synchronisation
   FR_TRY(m->conf.ensure(m->A, size_t(n_ub) * m->dim));
   FR_TRY(m->hang.ensure(m->A, size_t(n_ub) * m->nfc));
   FR_TRY(hcon.ensure(m->A, size_t(n_ub) * m->nfc * 4));
@@ -413,7 +428,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     T.mark(2);
     if (!r) {
       conn_dirty = true;
-      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon);
+      // issued without synchronisation: the edit's first kernel zeroed the face counter
+      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast);
     }
     if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -450,9 +450,18 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
 // d_fcnt (nullable): per leaf (n entries) the face-list counts, conforming faces owned (the + faces
 // of conforming pairs) in the low 32 bits and coarse sides of hanging faces in the high 32 bits;
 // zero past the device count
+// L (conf null: off): the face lists written by the connectivity kernel itself, each block's
+// faces appended at a base taken from *L.count (conforming count low 32 bits, hanging high), which
+// must hold zero; conf gets n*dim, hang n*2dim and hcon 4 x that entries at most
+struct FaceLists {
+  int32_t* conf = nullptr;
+  int32_t* hang = nullptr;
+  int32_t* hcon = nullptr;
+  unsigned long long* count = nullptr;
+};
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
-              Err* err, int64_t* d_fcnt = nullptr);
+              Err* err, int64_t* d_fcnt = nullptr, const FaceLists& L = FaceLists{});
 // sets *d_bad (not cleared here) unless keys are a complete sorted linear tree with depths in [Dlo, Dhi]
 int tree_validate_async(int dim, const KG& g, const uint64_t* d_keys, int64_t n, int Dlo, int Dhi,
                         int32_t* d_bad, cudaStream_t s, Err* err);

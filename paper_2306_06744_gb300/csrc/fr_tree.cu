@@ -605,7 +605,8 @@ __global__ void k_map(const uint64_t* __restrict__ old, int64_t no, const uint64
 template <int DIM>
 __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64_t* __restrict__ d_n, KG g,
                        int32_t* __restrict__ nbr, int8_t* __restrict__ ftype, int8_t* __restrict__ slot,
-                       int32_t* __restrict__ contrib, int32_t* bad, int64_t* __restrict__ fcnt) {
+                       int32_t* __restrict__ contrib, int32_t* bad, int64_t* __restrict__ fcnt,
+                       const FaceLists L) {
   pdl_wait_then_release();
   constexpr int NFC = 2 * DIM;
   // with fcnt: the block holds whole leaves (blockDim a multiple of 2*dim) and also writes each
@@ -619,6 +620,7 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
   if (fcnt) __syncthreads();
   const bool act = t < n_ub * NFC && t < n * NFC;
   int type = -1;
+  int32_t cv[4];  // the coarse side's contributors of a hanging face (fine leaves by slot)
   const int f = int(t % NFC);
   if (act) {
     const int64_t e = t / NFC;
@@ -654,6 +656,7 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
       slot[t] = 0;
       type = 2;
       int first = -1;
+      cv[2] = cv[3] = -1;  // 2 contributors in 2D
       for (int c = 0; c < (1 << DIM); ++c) {
         if (((c >> axis) & 1) != (side ? 0 : 1)) continue;
         uint64_t kc = child_key<DIM>(g, kN, c);
@@ -666,10 +669,48 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
         for (int b = 0; b < DIM; ++b)
           if (b != axis) sl |= ((c >> b) & 1) << sh++;
         if (sl == 0) first = int(m);
-        if (contrib) contrib[t * 4 + sl] = int32_t(m);
+        cv[sl] = int32_t(m);
       }
-      if (contrib && DIM == 2) contrib[t * 4 + 2] = contrib[t * 4 + 3] = -1;  // 2 contributors in 2D
+      if (contrib)
+        for (int r = 0; r < 4; ++r) contrib[t * 4 + r] = cv[r];
       nbr[t] = first;
+    }
+  }
+  if (L.conf) {
+    // the face lists themselves: a block's conforming faces it owns (its + faces) and coarse
+    // sides of hanging faces, in (leaf, face) order, appended at a base that one atomic per block
+    // takes from the packed counter (conforming low, hanging high).  The order of the blocks'
+    // ranges is arbitrary; every face's fluxes are computed and written by that face alone.
+    __shared__ int s_wc[8], s_wh[8];
+    __shared__ unsigned long long s_base;
+    const bool ec = (f & 1) && type == 0, eh = type == 2;
+    const unsigned lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const unsigned bc = __ballot_sync(0xFFFFFFFFu, ec), bh = __ballot_sync(0xFFFFFFFFu, eh);
+    const unsigned below = (1u << lane) - 1u;
+    if (lane == 0) {
+      s_wc[wid] = __popc(bc);
+      s_wh[wid] = __popc(bh);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long tc = 0, th = 0;
+      for (unsigned w = 0; w < (blockDim.x + 31u) / 32u; ++w) {
+        const int a = s_wc[w], b = s_wh[w];
+        s_wc[w] = int(tc);
+        s_wh[w] = int(th);
+        tc += unsigned(a);
+        th += unsigned(b);
+      }
+      s_base = (tc | th) ? atomicAdd(L.count, tc | (th << 32)) : 0ull;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+    const int64_t e = t / NFC;
+    if (ec) L.conf[int64_t(base & 0xFFFFFFFFull) + s_wc[wid] + __popc(bc & below)] = int32_t((e << 2) | (f >> 1));
+    if (eh) {
+      const int64_t h = int64_t(base >> 32) + s_wh[wid] + __popc(bh & below);
+      L.hang[h] = int32_t((e << 3) | f);
+      for (int r = 0; r < 4; ++r) L.hcon[h * 4 + r] = cv[r];
     }
   }
   if (!fcnt) return;
@@ -1054,13 +1095,13 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
 }
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,
-              Err* err, int64_t* d_fcnt) {
+              Err* err, int64_t* d_fcnt, const FaceLists& L) {
   if (n <= 0) return 0;
   const int64_t T = n * 2 * dim;
   // blocks of whole leaves: 64 leaves (2D, 256 threads) or 32 (3D, 192 threads)
   const int bt = dim == 2 ? 256 : 192;
   DIM_DISPATCH(dim, (launch_dependent(k_conn<D_>, nblk(T, bt), bt, s, d_keys, n, d_n, g, d_nbr, d_ftype, d_slot,
-                                      d_contrib, d_bad, d_fcnt)));
+                                      d_contrib, d_bad, d_fcnt, L)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
