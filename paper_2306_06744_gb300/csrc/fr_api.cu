@@ -35,7 +35,11 @@ struct fr_mesh {
   Buf<double> norm_part, norm_out;
   Buf<unsigned long long> dmax;
   Buf<float> mlp_params;  // learned indicator weights (FP32 master copy), empty if none
-  Buf<int32_t> status;    // device word set by a tensor-core kernel whose completion wait gave up
+  // device words read back together at the end of an adaptation: the adaptation's control block
+  // (CTL_SLOTS), its two error flags, and the status word a tensor-core kernel sets when its
+  // completion wait gave up
+  Buf<int64_t> ctlblk;
+  int32_t* status = nullptr;
   int64_t mlp_n = 0;
   // measurement: event pairs around interface (kind 0) and element (kind 1) launches
   struct Rec {
@@ -63,6 +67,8 @@ struct fr_mesh {
 namespace {
 
 constexpr int TB = 256;
+// the mesh's block of device words (fr_mesh::ctlblk): control block, error flags, status word
+constexpr int CTLBLK_BAD = CTL_SLOTS, CTLBLK_STATUS = CTL_SLOTS + 1, CTLBLK_WORDS = CTL_SLOTS + 2;
 inline unsigned nblk(int64_t n, int b = TB) { return unsigned((n + b - 1) / b); }
 
 template <int DIM>
@@ -285,7 +291,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.a = a;
   S.b = b;
   S.c = c;
-  S.status = m->status.p;
+  S.status = m->status;
   S.flags = flags;
   S.th_r = m->cfg.th_refine;
   S.th_c = m->cfg.th_coarsen;
@@ -329,7 +335,7 @@ int compute_flags(fr_mesh* m, double* eta) {
     if (!X) return set_error(&m->err, FR_ENOMEM, "feature scratch");
     FR_TRY(mlp_features(m->dim, m->p, m->u.p, m->keys.p, m->M, m->g, m->cfg.Dbase, m->cfg.gamma,
                         m->ops, X, m->stream, &m->err));
-    return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->status.p, m->stream, &m->err);
+    return mlp_forward(m->mlp_params.p, in, X, m->M, nullptr, m->flags.p, m->status, m->stream, &m->err);
   }
   // flags the last time step already wrote for the current state
   if (m->cfg.indicator == 0 && !eta && m->flags_fresh) return 0;
@@ -383,11 +389,9 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   const int64_t M0 = m->M;
   int64_t n_ub = M0 << m->dim;
   bool fast = transfer && n_ub + int64_t(m->g.Dmax) * 4096 <= FAST_ADAPT_MAX;
-  Scratch Sc(&m->A);
-  int64_t* ctl = Sc.get<int64_t>(CTL_SLOTS);
-  int32_t* bad = Sc.get<int32_t>(2);
-  if (!ctl || !bad) return set_error(err, FR_ENOMEM, "adapt scratch");
-  int64_t h_ctl[CTL_SLOTS] = {0};
+  int64_t* ctl = m->ctlblk.p;
+  int32_t* bad = reinterpret_cast<int32_t*>(ctl + CTLBLK_BAD);
+  int64_t h_ctl[CTLBLK_WORDS] = {0};
   int32_t hb[2] = {0, 0}, hs = 0;
   Buf<uint64_t> nk;
   Buf<double> nu;
@@ -398,14 +402,17 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   // the traces of unchanged elements are carried over by the transfer (when the current ones are
   // valid); only refined and fused elements get theirs computed afterwards
   const bool carry = transfer && m->traces_ok;
-  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err);
+  // issued without synchronisation, the edit and the balance passes carry each new leaf's origin
+  // in the old tree (src) and its relation to it (tag): the old->new mapping of Sec. 4.2 without a
+  // search
+  int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err,
+                     fast ? &src : nullptr, fast ? &tag : nullptr);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
     int r = 0;
     if (transfer) {
-      // small meshes (issued without synchronisation, where launches set the cost): the mapping
-      // (Sec. 4.2) runs inside the transfer kernel, block by block; large meshes map first with
-      // one thread per new leaf, which keeps the transfer's blocks off the search latency
+      // large meshes (and a fast path that fell back to exact sizes) map the new leaves with one
+      // search per leaf; otherwise src and tag came with the balanced tree
       if (!fast) {
         if (!r) r = src.ensure(m->A, nb);
         if (!r) r = tag.ensure(m->A, nb);
@@ -420,8 +427,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
         tc = TraceCopy{m->trace.p, ntr.p, retr.p, m->EF * trace_elem_bytes(m->cfg.precision)};
       }
       if (!r)
-        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, fast ? nullptr : src.p, fast ? nullptr : tag.p,
-                            bad + 1, nb, d_n, m->ops, m->u.p, nu.p, tc, s, err);
+        r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, src.p, tag.p, bad + 1, nb, d_n, m->ops, m->u.p,
+                            nu.p, tc, s, err);
     } else {
       T.mark(1);
     }
@@ -431,20 +438,27 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       // issued without synchronisation: the edit's first kernel zeroed the face counter
       r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast);
     }
+    // the traces of the refined and fused elements (the others were carried), before the
+    // synchronisation, against the device leaf count
+    if (!r && carry)
+      r = launch_traces(m->cfg.precision, m->dim, m->p, nu.p, nb, m->ops, ntr.p, s, err, retr.p, d_n);
+    // one copy: the control block, the error flags and the status word are adjacent
     if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-               cudaMemcpyAsync(hb, bad, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-               cudaMemcpyAsync(&hs, m->status.p, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                cudaStreamSynchronize(s) != cudaSuccess))
       r = set_error(err, FR_ECUDA, "adapt read");
+    if (!r) {
+      std::memcpy(hb, &h_ctl[CTLBLK_BAD], sizeof(hb));
+      std::memcpy(&hs, &h_ctl[CTLBLK_STATUS], sizeof(hs));
+    }
     if (!r && hs) {
       r = set_error(err, FR_ETIMEOUT, "a tensor-core completion wait gave up (indicator or element kernel)");
       // reported once: the status word starts clear for the next call
-      if (cudaMemsetAsync(m->status.p, 0, 4, s) != cudaSuccess) cudaGetLastError();
+      if (cudaMemsetAsync(m->status, 0, 4, s) != cudaSuccess) cudaGetLastError();
     }
     return r;
   };
   if (!rc && fast) {
-    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err);
+    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err, &src, &tag);
     if (!rc) rc = rest(n_ub, ctl + CTL_N);
     if (!rc && h_ctl[CTL_OVER] != 0) {
       // a balance pass generated more octants than the issued passes hold: finish the balance
@@ -508,7 +522,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   m->flags_fresh = false;
   rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
   hcon.release(m->A);
-  if (!rc && transfer) rc = refresh_traces(m, carry ? retr.p : nullptr);
+  if (!rc && carry) m->traces_ok = true;  // computed before the synchronisation
+  if (!rc && transfer && !carry) rc = refresh_traces(m);
   retr.release(m->A);
   FR_TRY(rc);
   T.mark(3);
@@ -571,8 +586,9 @@ int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void*
   }
   // uniform tree at Dbase, then passes of {closed form, flags, adapt}
   m->M = int64_t(1) << (m->dim * cfg->Dbase);
-  FR_TRY(m->status.ensure(m->A, 1));
-  FR_CUDA(err, cudaMemsetAsync(m->status.p, 0, 4, m->stream));
+  FR_TRY(m->ctlblk.ensure(m->A, CTLBLK_WORDS));
+  FR_CUDA(err, cudaMemsetAsync(m->ctlblk.p, 0, CTLBLK_WORDS * sizeof(int64_t), m->stream));
+  m->status = reinterpret_cast<int32_t*>(m->ctlblk.p + CTLBLK_STATUS);
   FR_TRY(m->keys.ensure(m->A, m->M));
   FR_TRY(tree_uniform(m->dim, m->g, cfg->Dbase, m->keys.p, m->stream, err));
   FR_TRY(ensure_state(m, m->M));
@@ -622,7 +638,8 @@ void free_all(fr_mesh* m) {
   m->norm_out.release(m->A);
   m->dmax.release(m->A);
   m->mlp_params.release(m->A);
-  m->status.release(m->A);
+  m->ctlblk.release(m->A);
+  m->status = nullptr;
   m->A.release_cache();
   // blocks still handed out (none after a clean release) go back to the allocator as well
   auto live = m->cache.live;

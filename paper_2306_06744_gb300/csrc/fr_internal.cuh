@@ -427,10 +427,11 @@ enum {
 };
 // The edit zeroes the control block (and the two error flags d_bad, if given) and leaves its
 // leaf count and statistics there without a host synchronisation; its output holds at most
-// n << dim leaves.
+// n << dim leaves.  With org/otg: each edited leaf's origin in the old tree and its relation to
+// it (0 the same leaf, 1 inside it, 2 the parent of the 2^dim old leaves from the origin on).
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
               int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
-              Err* err);
+              Err* err, Buf<int32_t>* org = nullptr, Buf<int8_t>* otg = nullptr);
 // balances `keys` in place for depth passes D = Dhigh .. Dlow with exact sizes (one host
 // synchronisation per pass); the leaf count is d_ctl[0] on entry (at most n_ub) and h_ctl
 // (CTL_SLOTS values) holds the final control block on return
@@ -439,9 +440,12 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 // the same passes (Dmax .. Dlow) issued without any host synchronisation: each pass may generate
 // at most 4096 octants, *n_ub is raised to a bound of the final leaf count, and a pass that would
 // generate more sets d_ctl[4] to its depth and leaves the tree unchanged from there on (the caller
-// then finishes with tree_balance from that depth)
+// then finishes with tree_balance from that depth).  With org/otg (those of the edit): carried
+// through the passes, so that they give every leaf of the balanced tree its origin in the tree
+// before the edit and its relation to it, as the old->new mapping (tree_map) would.
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
-                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err);
+                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org = nullptr,
+                       Buf<int8_t>* otg = nullptr);
 // d_n_new / d_n (nullable): device leaf count of the new tree; n_new / n is then an upper bound
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
              int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,

@@ -160,14 +160,17 @@ __device__ __forceinline__ ff cst<ff>(double x) {
 template <int DIM, int NP, class T>
 __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_traces_t(const double* __restrict__ u, int64_t M,
                                                               const __grid_constant__ OpsT<T> ops,
-                                                              T* __restrict__ tr, const int8_t* __restrict__ mask) {
+                                                              T* __restrict__ tr, const int8_t* __restrict__ mask,
+                                                              const int64_t* __restrict__ d_M) {
   pdl_wait_then_release();
   using S = Sz<DIM, NP>;
   constexpr int N = S::N, NV = S::NV, NF = S::NF, EU = S::EU, EF = S::EF, EPB = S::EPB;
   constexpr int FQ = S::NFC * NF;
   __shared__ T su[EPB * EU];
   __shared__ int8_t need[EPB];
+  if (d_M && *d_M < M) M = *d_M;  // the element count on the device (M is then a bound of it)
   const int64_t e0 = int64_t(blockIdx.x) * EPB;
+  if (e0 >= M) return;
   const int ne = int((M - e0) < EPB ? (M - e0) : EPB);
   if (threadIdx.x < ne) need[threadIdx.x] = mask ? mask[e0 + threadIdx.x] : 1;
   __syncthreads();
@@ -594,13 +597,13 @@ inline int ipow_k(int b, int e) {
 
 template <class T>
 int launch_traces_impl(int dim, int p, const double* u, int64_t M, const DevOps& o, void* tr,
-                       const int8_t* mask, cudaStream_t s, Err* err) {
+                       const int8_t* mask, cudaStream_t s, Err* err, const int64_t* d_M) {
   if (M <= 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    const unsigned nb = unsigned((M + SS::EPB - 1) / SS::EPB);
-                   launch_dependent(k_traces_t<DD, NN, T>, nb, SS::BT, s, u, M, ops, static_cast<T*>(tr), mask);
+                   launch_dependent(k_traces_t<DD, NN, T>, nb, SS::BT, s, u, M, ops, static_cast<T*>(tr), mask, d_M);
                  }));
   FR_LAUNCH_CHECK(err);
   return 0;

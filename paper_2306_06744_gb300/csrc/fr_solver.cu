@@ -516,10 +516,10 @@ int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, d
 }
 
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
-                  cudaStream_t s, Err* err, const int8_t* mask) {
-  if (prec >= 1 && prec <= 3) return launch_traces_f32(dim, p, u, M, ops, tr, mask, s, err);
-  if (prec == 4) return launch_traces_ff(dim, p, u, M, ops, tr, mask, s, err);
-  return launch_traces_f64(dim, p, u, M, ops, tr, mask, s, err);
+                  cudaStream_t s, Err* err, const int8_t* mask, const int64_t* d_M) {
+  if (prec >= 1 && prec <= 3) return launch_traces_f32(dim, p, u, M, ops, tr, mask, s, err, d_M);
+  if (prec == 4) return launch_traces_ff(dim, p, u, M, ops, tr, mask, s, err, d_M);
+  return launch_traces_f64(dim, p, u, M, ops, tr, mask, s, err, d_M);
 }
 
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err) {

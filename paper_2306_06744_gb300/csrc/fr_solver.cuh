@@ -36,9 +36,10 @@ int launch_exact(int dim, int p, const uint64_t* keys, int64_t M, const KG& g, d
                  const DevProblem& P, const DevOps& ops, double* u, cudaStream_t s, Err* err);
 // prec: 0 FP64, 1 FP32 with FP64 Runge-Kutta combination, 2 TF32 and 3 bf16x3 tensor-core
 // derivative (otherwise as 1; 3D p = 3), 4 double-word (two floats).  mask (nullable): traces only
-// of the elements with a non-zero entry
+// of the elements with a non-zero entry.  d_M (nullable): the element count on the device, M is then
+// a bound of it
 int launch_traces(int prec, int dim, int p, const double* u, int64_t M, const DevOps& ops, void* tr,
-                  cudaStream_t s, Err* err, const int8_t* mask = nullptr);
+                  cudaStream_t s, Err* err, const int8_t* mask = nullptr, const int64_t* d_M = nullptr);
 // bytes of one element's traces in the arithmetic type of `prec`
 inline int trace_elem_bytes(int prec) { return (prec >= 1 && prec <= 3) ? 4 : 8; }
 int launch_faces(int prec, int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s, Err* err);
@@ -47,7 +48,8 @@ int launch_stage(int prec, int dim, int p, const StageArgs& A, const DevOps& ops
 // per-precision instantiations (fr_prec_f64.cu, fr_prec_f32.cu, fr_prec_ff.cu)
 #define FR_DECLARE_PREC(sfx)                                                                    \
   int launch_traces_##sfx(int dim, int p, const double* u, int64_t M, const DevOps& ops,        \
-                          void* tr, const int8_t* mask, cudaStream_t s, Err* err);              \
+                          void* tr, const int8_t* mask, cudaStream_t s, Err* err,               \
+                          const int64_t* d_M);                                                  \
   int launch_faces_##sfx(int dim, int p, FaceArgs A, const DevOps& ops, cudaStream_t s,         \
                          Err* err);                                                             \
   int launch_stage_##sfx(int dim, int p, const StageArgs& A, const DevOps& ops, cudaStream_t s, \

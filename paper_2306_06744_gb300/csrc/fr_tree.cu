@@ -100,7 +100,7 @@ __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __res
 template <int DIM>
 __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __restrict__ act,
                              const Offs O, int64_t n, KG g, uint64_t* __restrict__ out,
-                             unsigned long long* stats) {
+                             unsigned long long* stats, int32_t* __restrict__ org, int8_t* __restrict__ otg) {
   pdl_wait_then_release();
   int64_t grand;
   const int64_t base = offs_base(O, int64_t(blockIdx.x) * blockDim.x, &grand);
@@ -108,7 +108,8 @@ __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __res
   if (i >= n) return;
   uint64_t key = k[i];
   int64_t o = O.offs[i] + base;
-  switch (act[i]) {
+  const int a = act[i];
+  switch (a) {
     case 0: out[o] = key; break;
     case 1:
       for (int c = 0; c < (1 << DIM); ++c) out[o + c] = child_key<DIM>(g, key, c);
@@ -119,6 +120,14 @@ __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __res
       atomicAdd(&stats[1], 1ull);
       break;
     default: break;
+  }
+  if (org && a != 3) {
+    // the origin: this leaf (kept, refined) or the family's first child (fused)
+    const int nc = a == 1 ? (1 << DIM) : 1;
+    for (int c = 0; c < nc; ++c) {
+      org[o + c] = int32_t(i);
+      otg[o + c] = int8_t(a);
+    }
   }
 }
 
@@ -442,20 +451,29 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
   if (nS <= RANK_SORT_MAX) {
     // rank sort: each key's position is the number of smaller keys plus the equal keys before it
     uint64_t mine = 0;
+    int r = 0;
     if (t < nS) mine = sk[t] = S[t];
     __syncthreads();
-    if (t < nS) {
-      int r = 0;
+    if (t < nS)
       for (int j = 0; j < nS; ++j) {
         const uint64_t o = sk[j];
         r += (o < mine) || (o == mine && j < t);
       }
-      S[r] = mine;
-    }
+    __syncthreads();  // every rank is taken before the keys move
+    if (t < nS) sk[r] = mine;
   } else {
     int Pw = 1;
     while (Pw < nS) Pw <<= 1;
-    for (int i = t; i < Pw; i += blockDim.x) sk[i] = i < nS ? S[i] : ~0ull;
+    // up to four loads in flight per thread (Pw <= 4 x blockDim)
+    uint64_t v[SMALL_SORT_MAX / 1024];
+#pragma unroll
+    for (int q = 0; q < SMALL_SORT_MAX / 1024; ++q) {
+      const int i = t + q * 1024;
+      v[q] = i < nS ? S[i] : ~0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < SMALL_SORT_MAX / 1024; ++q)
+      if (t + q * 1024 < Pw) sk[t + q * 1024] = v[q];
     __syncthreads();
     for (int kk = 2; kk <= Pw; kk <<= 1) {
       for (int j = kk >> 1; j > 0; j >>= 1) {
@@ -477,21 +495,20 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
           __syncwarp();
       }
     }
-    for (int i = t; i < nS; i += blockDim.x) S[i] = sk[i];
   }
-  __syncthreads();  // the sorted octants are in S (global writes of this block are visible now)
+  __syncthreads();  // the sorted octants are in sk
   // per thread 4 consecutive octants r = 4t .. 4t+3: kept(r) - first(r), with first(r) when the
   // containing leaf of r differs from that of r - 1
   // (packed: the containing leaf is the value's low bits, the key its high bits; the sorted keys
-  // are written back unpacked once every thread has read its neighbours)
+  // are written back to S unpacked)
   const uint64_t lmask = (1ull << PACK_BITS) - 1;
   auto leaf_of = [&](int r) -> int64_t {
-    return packed ? int64_t(S[r] & lmask) : upper_bound_dev(k, n, S[r]) - 1;
+    return packed ? int64_t(sk[r] & lmask) : upper_bound_dev(k, n, sk[r]) - 1;
   };
   auto keep_of = [&](int r) -> bool {
-    if (!packed) return lin_keep<DIM>(S, nS, g, r);
+    if (!packed) return lin_keep<DIM>(sk, nS, g, r);
     if (r + 1 >= nS) return true;
-    const uint64_t a = S[r] >> PACK_BITS, b = S[r + 1] >> PACK_BITS;
+    const uint64_t a = sk[r] >> PACK_BITS, b = sk[r + 1] >> PACK_BITS;
     return !(a == b || is_ancestor<DIM>(g, a, b));
   };
   int v[4], sum = 0;
@@ -508,11 +525,10 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
     }
     sum += v[q];
   }
-  if (packed) {
-    __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (4 * t + q < nS) S[4 * t + q] >>= PACK_BITS;
+  for (int q = 0; q < 4; ++q) {
+    const int r = 4 * t + q;
+    if (r < nS) S[r] = packed ? sk[r] >> PACK_BITS : sk[r];
   }
   // block-wide exclusive scan of the per-thread sums
   const int lane = t & 31, wid = t >> 5;
@@ -561,22 +577,45 @@ __device__ __forceinline__ int lower_bound_sh(const uint64_t* a, int n, uint64_t
   }
   return lo;
 }
+// With oi/ti (origin and relation of each leaf to the tree before the edit, tree_edit): the same
+// for the merged tree into oo/to.  An octant inside leaf X lies inside X's origin (relation 1),
+// unless X is a fused parent: then the octant is, or lies inside, the old child that contains it.
 template <int DIM>
 __global__ void k_merge_fast(const uint64_t* __restrict__ k, const int64_t* __restrict__ ctl, int64_t n_ub,
                              const uint64_t* __restrict__ S, const int32_t* __restrict__ P, KG g,
-                             uint64_t* __restrict__ out) {
+                             uint64_t* __restrict__ out, const int32_t* __restrict__ oi,
+                             const int8_t* __restrict__ ti, int32_t* __restrict__ oo, int8_t* __restrict__ to) {
   pdl_wait_then_release();
   __shared__ uint64_t sS[SMALL_SORT_MAX];
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n = ctl[CTL_NPREV];
   const int nS = int(ctl[CTL_GS]);  // at most SMALL_SORT_MAX (the sort kernel's capacity check)
   if (int64_t(blockIdx.x) * blockDim.x >= n) return;  // the whole block is past the leaves
-  for (int r = threadIdx.x; r < nS; r += blockDim.x) sS[r] = S[r];
+  // eight loads in flight per thread before their stores
+  for (int r0 = threadIdx.x; r0 < nS; r0 += 8 * blockDim.x) {
+    uint64_t v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = r0 + q * int(blockDim.x);
+      v[q] = r < nS ? S[r] : 0ull;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int r = r0 + q * int(blockDim.x);
+      if (r < nS) sS[r] = v[q];
+    }
+  }
   __syncthreads();
   if (i >= n_ub || i >= n) return;
   const uint64_t key = k[i];
+  const int32_t src = oo ? oi[i] : 0;
+  const int tag = oo ? ti[i] : 0;
   if (nS == 0) {
     out[i] = key;
+    if (oo) {
+      oo[i] = src;
+      to[i] = int8_t(tag);
+    }
     return;
   }
   const int64_t lo = lower_bound_sh(sS, nS, key);
@@ -584,10 +623,30 @@ __global__ void k_merge_fast(const uint64_t* __restrict__ k, const int64_t* __re
   int64_t o = i + P[lo];
   if (hi == lo) {
     out[o] = key;
+    if (oo) {
+      oo[o] = src;
+      to[o] = int8_t(tag);
+    }
     return;
   }
+  const int d1 = g.depth(key) + 1;
   for (int64_t r = lo; r < hi; ++r)
-    if (lin_keep<DIM>(sS, nS, g, r)) out[o++] = sS[r];
+    if (lin_keep<DIM>(sS, nS, g, r)) {
+      const uint64_t y = sS[r];
+      out[o] = y;
+      if (oo) {
+        if (tag == 2) {
+          const uint64_t span = vol_raw<DIM>(g, d1);
+          const int c = child_index<DIM>(g, g.make(g.raw(y) / span * span, d1));
+          oo[o] = src + c;
+          to[o] = int8_t(g.depth(y) == d1 ? 0 : 1);
+        } else {
+          oo[o] = src;
+          to[o] = 1;
+        }
+      }
+      ++o;
+    }
 }
 
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
@@ -919,7 +978,7 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys, int64_t n, Buf<uint64
 
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
               int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
-              Err* err) {
+              Err* err, Buf<int32_t>* org, Buf<int8_t>* otg) {
   Scratch S(&A);
   int8_t* act = S.get<int8_t>(n);
   int32_t* cnt = S.get<int32_t>(n);
@@ -933,8 +992,13 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   FR_LAUNCH_CHECK(err);
   Offs O;
   FR_TRY(scan_counts_local(cnt, offs, n, d_ctl + CTL_N, S, s, err, &O));
+  if (org) {
+    FR_TRY(org->ensure(A, size_t(n) << dim));
+    FR_TRY(otg->ensure(A, size_t(n) << dim));
+  }
   DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, O, n, g, out.p,
-                                                               reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF))));
+                                      reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF),
+                                      org ? org->p : nullptr, org ? otg->p : nullptr)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
@@ -1047,8 +1111,11 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 }
 
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
-                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err) {
+                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org,
+                       Buf<int8_t>* otg) {
   Buf<uint64_t> gen, out;
+  Buf<int32_t> org_out;
+  Buf<int8_t> otg_out;
   int rc = 0;
   const int64_t cap = SMALL_SORT_MAX;
   for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
@@ -1057,7 +1124,8 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
     // key bits and the containing leaf's index fit one 64-bit value
     const bool packed = dim * g.Dmax + g.mb + PACK_BITS <= 64 && nb < (int64_t(1) << PACK_BITS);
     int32_t* P = S.get<int32_t>(cap + 1);
-    if (!P || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap))) {
+    if (!P || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap)) ||
+        (org && (org_out.ensure(A, size_t(nb + cap)) || otg_out.ensure(A, size_t(nb + cap))))) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
@@ -1069,7 +1137,10 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
     ++launch_counter();
     DIM_DISPATCH(dim, (launch_dependent(k_merge_fast<D_>, nblk(nb), TB, s, static_cast<const uint64_t*>(keys.p),
                                         static_cast<const int64_t*>(d_ctl), nb, static_cast<const uint64_t*>(gen.p),
-                                        static_cast<const int32_t*>(P), g, out.p)));
+                                        static_cast<const int32_t*>(P), g, out.p,
+                                        static_cast<const int32_t*>(org ? org->p : nullptr),
+                                        static_cast<const int8_t*>(org ? otg->p : nullptr),
+                                        org ? org_out.p : nullptr, org ? otg_out.p : nullptr)));
     ++launch_counter();
     if (cudaGetLastError() != cudaSuccess) {
       rc = set_error(err, FR_ECUDA, "balance pass launch");
@@ -1078,10 +1149,16 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
     Buf<uint64_t> t = keys;  // the merged tree becomes the tree
     keys = out;
     out = t;
+    if (org) {
+      std::swap(*org, org_out);
+      std::swap(*otg, otg_out);
+    }
     *n_ub = nb + cap;
   }
   gen.release(A);
   out.release(A);
+  org_out.release(A);
+  otg_out.release(A);
   return rc;
 }
 

@@ -12,6 +12,7 @@ import pytest
 import oracle as O
 from paper_2306_06744_gb300 import fr
 from paper_2306_06744_gb300 import workloads as W
+from tests import brute
 
 pytestmark = pytest.mark.gpu
 
@@ -159,6 +160,61 @@ def test_transfer_parity(dim, p, Dbase, Dmax):
     o.adapt(flags)
     assert np.array_equal(g.leaves(), o.leaves())
     assert rel_l2(g.state(), o.state()) < 1e-13
+
+
+def _resplit_fused(dim, Dmax, Dbase, keys, flags, new_keys):
+    """Counts of new leaves that lie strictly inside a parent the edit fused (the balance split it
+    again): at the children's depth (the old leaves themselves) and deeper (inside one of them)."""
+    ob = [tuple(int(v) for v in b) for b in O.morton_decode(dim, Dmax, keys)]
+    _, fused = brute.edit(dim, Dmax, Dbase, ob, flags)
+    new = [tuple(int(v) for v in b) for b in O.morton_decode(dim, Dmax, new_keys)]
+    same = deeper = 0
+    for F in fused:
+        for b in new:
+            if b != F and brute.contains(Dmax, F, b):
+                same += b[0] == F[0] + 1
+                deeper += b[0] >= F[0] + 2
+    return same, deeper
+
+
+@pytest.mark.parametrize("dim,p,Dbase,Dmax", [(2, 3, 2, 6), (3, 2, 1, 5)])
+def test_transfer_through_fused_parents_split_again(dim, p, Dbase, Dmax):
+    # Sec. 4.2 mapping on a tree whose edit fuses families next to refined leaves, so that the
+    # 2:1 balance splits some fused parents again: into the old children themselves (a copy of
+    # each) and below them (prolongation from the old child that contains the new leaf).  The
+    # adaptation derives each new leaf's source while it edits and balances; the oracle searches
+    # the old tree.  Leaves and state must agree; both kinds of re-split must occur.
+    cfg = _cfg("vortex2d_p2_small" if dim == 2 else "vortex3d_p2_tube", dim=dim, p=p, Dbase=Dbase,
+               Dmax=Dmax, init_passes=0, indicator=2, dt=1e-3)
+    seen = np.zeros(2, dtype=int)
+    for seed in range(40):
+        keys = _random_tree(dim, Dbase, Dmax, 300 + seed, psplit=0.45)
+        M = len(keys)
+        ob = [tuple(int(v) for v in b) for b in O.morton_decode(dim, Dmax, keys)]
+        pos = {b: i for i, b in enumerate(ob)}
+        flags = W.random_flags(M, 500 + seed, p_refine=0.3, p_coarsen=0.0)
+        coin = W.random_uniform(M, 700 + seed)
+        for i, b in enumerate(ob):  # complete sibling families, all flagged for coarsening
+            if b[0] <= Dbase or coin[i] > 0.5:
+                continue
+            kids = brute.children(dim, Dmax, brute.parent(Dmax, b))
+            if kids[0] == b and all(k in pos for k in kids):
+                for k in kids:
+                    flags[pos[k]] = -1
+        u = _smooth_state(cfg, keys, seed)
+        g = fr.Mesh(cfg)
+        o = O.OracleMesh(cfg)
+        g.set_state(keys, u)
+        o.set_state(keys, u)
+        g.adapt(flags)
+        o.adapt(flags)
+        assert np.array_equal(g.leaves(), o.leaves()), seed
+        assert rel_l2(g.state(), o.state()) < 1e-13, seed
+        g.close()
+        seen += _resplit_fused(dim, Dmax, Dbase, keys, flags, o.leaves())
+        if (seen > 0).all() and seed >= 3:
+            break
+    assert (seen > 0).all(), ("the trees never split a fused parent again", seen)
 
 
 def test_run_is_deterministic():
