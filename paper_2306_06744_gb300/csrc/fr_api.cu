@@ -1,6 +1,8 @@
 // fr_api.cu -- the C ABI of include/fr.h: mesh object, time stepping, adaptation orchestration
 // (flags -> edit -> 2:1 balance -> mapping -> transfer -> connectivity), face lists, host I/O and
 // the device-array tree primitives.
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 
@@ -40,6 +42,11 @@ struct fr_mesh {
   // completion wait gave up
   Buf<int64_t> ctlblk;
   int32_t* status = nullptr;
+  // pinned host words mapped for the device: the adaptation's connectivity kernel publishes the
+  // ctlblk words there followed by a sequence number (null: read back by copy and synchronise)
+  int64_t* pub_h = nullptr;
+  int64_t* pub_d = nullptr;
+  int64_t pub_seq = 0;
   int64_t mlp_n = 0;
   // measurement: event pairs around interface (kind 0) and element (kind 1) launches
   struct Rec {
@@ -123,8 +130,10 @@ int check_cfg(const fr_config* c, Err* err) {
 // append: *d_faces holds zero and the connectivity kernel appends the faces to the lists itself
 // (one launch; the lists' order then varies from run to run, the fluxes do not); otherwise the
 // lists are written in leaf order after a scan of the per-leaf counts.
+// seq > 0 (append only): the kernel also publishes the mesh's ctlblk words to its mapped host words
+// with this sequence number.
 static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int64_t* d_n, int64_t* d_faces,
-                      int32_t* bad, Buf<int32_t>& hcon, bool append = false) {
+                      int32_t* bad, Buf<int32_t>& hcon, bool append = false, int64_t seq = 0) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
   const int64_t S = n_ub * m->nfc;
@@ -142,6 +151,13 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
     L.hang = m->hang.p;
     L.hcon = hcon.p;
     L.count = reinterpret_cast<unsigned long long*>(d_faces);
+    if (seq > 0 && m->pub_d) {
+      L.pub = m->pub_d;
+      L.words = m->ctlblk.p;
+      L.nwords = CTLBLK_WORDS;
+      L.seq = seq;
+      L.done = reinterpret_cast<unsigned long long*>(m->ctlblk.p + CTL_DONE);
+    }
     return tree_conn(m->dim, m->g, keys, n_ub, d_n, m->nbr.p, m->ftype.p, m->slot.p, nullptr, bad, s, err,
                      nullptr, L);
   }
@@ -164,6 +180,33 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
     launch_dependent(k_face_write<3>, nblk(n_ub), TB, s, static_cast<const int8_t*>(m->ftype.p),
                      static_cast<const int32_t*>(m->contrib.p), n_ub, d_n, O, m->conf.p, m->hang.p, hcon.p);
   FR_LAUNCH_CHECK(err);
+  return 0;
+}
+
+// Waits for the publication `seq` of the connectivity kernel (conn_issue) and copies the ctlblk
+// words into h: a host spin on the mapped sequence word, with a stream query every 1024 reads
+// (an error, or a finished stream without the publication, ends it) and a 60 s bound.
+static int wait_published(fr_mesh* m, int64_t seq, int64_t* h) {
+  const volatile int64_t* p = m->pub_h;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint64_t it = 1;; ++it) {
+    if (p[CTLBLK_WORDS] == seq) break;
+    if ((it & 1023) == 0) {
+      const cudaError_t q = cudaStreamQuery(m->stream);
+      if (q == cudaSuccess) {
+        if (p[CTLBLK_WORDS] == seq) break;
+        return set_error(&m->err, FR_ECUDA, "adapt: the counts were not published");
+      }
+      if (q != cudaErrorNotReady) {
+        cudaGetLastError();
+        return set_error(&m->err, FR_ECUDA, "adapt read");
+      }
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60))
+        return set_error(&m->err, FR_ECUDA, "adapt: no publication of the counts within 60 s");
+    }
+  }
+  std::atomic_thread_fence(std::memory_order_acquire);
+  for (int w = 0; w < CTLBLK_WORDS; ++w) h[w] = p[w];
   return 0;
 }
 
@@ -433,19 +476,25 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       T.mark(1);
     }
     T.mark(2);
+    int64_t seq = 0;
     if (!r) {
       conn_dirty = true;
-      // issued without synchronisation: the edit's first kernel zeroed the face counter
-      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast);
+      // issued without synchronisation: the edit's first kernel zeroed the face counter and the
+      // finished-block counter; the last block publishes the counts to mapped host memory
+      seq = (fast && m->pub_h) ? ++m->pub_seq : 0;
+      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast, seq);
     }
     // the traces of the refined and fused elements (the others were carried), before the
     // synchronisation, against the device leaf count
     if (!r && carry)
       r = launch_traces(m->cfg.precision, m->dim, m->p, nu.p, nb, m->ops, ntr.p, s, err, retr.p, d_n);
-    // one copy: the control block, the error flags and the status word are adjacent
-    if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-               cudaStreamSynchronize(s) != cudaSuccess))
+    // one read: the control block, the error flags and the status word are adjacent
+    if (!r && seq > 0) {
+      r = wait_published(m, seq, h_ctl);
+    } else if (!r && (cudaMemcpyAsync(h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                      cudaStreamSynchronize(s) != cudaSuccess)) {
       r = set_error(err, FR_ECUDA, "adapt read");
+    }
     if (!r) {
       std::memcpy(hb, &h_ctl[CTLBLK_BAD], sizeof(hb));
       std::memcpy(&hs, &h_ctl[CTLBLK_STATUS], sizeof(hs));
@@ -589,6 +638,20 @@ int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void*
   FR_TRY(m->ctlblk.ensure(m->A, CTLBLK_WORDS));
   FR_CUDA(err, cudaMemsetAsync(m->ctlblk.p, 0, CTLBLK_WORDS * sizeof(int64_t), m->stream));
   m->status = reinterpret_cast<int32_t*>(m->ctlblk.p + CTLBLK_STATUS);
+  {
+    // without mapped host memory the adaptation reads its counts back by a copy instead
+    void* hp = nullptr;
+    void* dp = nullptr;
+    if (cudaHostAlloc(&hp, (CTLBLK_WORDS + 1) * sizeof(int64_t), cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&dp, hp, 0) == cudaSuccess) {
+      std::memset(hp, 0, (CTLBLK_WORDS + 1) * sizeof(int64_t));
+      m->pub_h = static_cast<int64_t*>(hp);
+      m->pub_d = static_cast<int64_t*>(dp);
+    } else {
+      if (hp) cudaFreeHost(hp);
+      cudaGetLastError();
+    }
+  }
   FR_TRY(m->keys.ensure(m->A, m->M));
   FR_TRY(tree_uniform(m->dim, m->g, cfg->Dbase, m->keys.p, m->stream, err));
   FR_TRY(ensure_state(m, m->M));
@@ -619,6 +682,13 @@ int init_impl(fr_mesh* m, const fr_config* cfg, const fr_allocator* alloc, void*
   m->step = 0;
   FR_CUDA(err, cudaStreamSynchronize(m->stream));
   return 0;
+}
+
+// the mapped host words, once the stream has finished (a kernel may still publish to them)
+void free_pub(fr_mesh* m) {
+  cudaStreamSynchronize(m->stream);
+  if (m->pub_h) cudaFreeHost(m->pub_h);
+  m->pub_h = m->pub_d = nullptr;
 }
 
 void free_all(fr_mesh* m) {
@@ -679,6 +749,7 @@ int fr_mesh_init(const fr_config* cfg, const fr_allocator* alloc, void* stream, 
   if (rc) {
     *global_err() = m->err;
     free_all(m);
+    free_pub(m);
     delete m;
     return rc;
   }
@@ -689,7 +760,7 @@ int fr_mesh_init(const fr_config* cfg, const fr_allocator* alloc, void* stream, 
 void fr_mesh_free(fr_mesh* m) {
   if (!m) return;
   free_all(m);
-  cudaStreamSynchronize(m->stream);
+  free_pub(m);
   for (cudaEvent_t e : m->ev_pool) cudaEventDestroy(e);
   delete m;
 }

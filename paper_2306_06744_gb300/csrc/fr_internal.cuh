@@ -420,10 +420,10 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf
 // [2] refined leaves, [3] coarsened groups, [4] overflowed pass depth (0: none), [5] passes that
 // changed the tree, [6] face-list counts (conforming | hanging << 32); for the merge of a balance
 // pass issued without synchronisation: [7] the leaf count before the pass, [8] the sorted
-// octants it merges.
+// octants it merges; [9] blocks of the connectivity kernel that have finished (FaceLists::pub).
 enum {
   CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6,
-  CTL_NPREV = 7, CTL_GS = 8, CTL_SLOTS = 10
+  CTL_NPREV = 7, CTL_GS = 8, CTL_DONE = 9, CTL_SLOTS = 10
 };
 // The edit zeroes the control block (and the two error flags d_bad, if given) and leaves its
 // leaf count and statistics there without a host synchronisation; its output holds at most
@@ -456,12 +456,20 @@ int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const u
 // zero past the device count
 // L (conf null: off): the face lists written by the connectivity kernel itself, each block's
 // faces appended at a base taken from *L.count (conforming count low 32 bits, hanging high), which
-// must hold zero; conf gets n*dim, hang n*2dim and hcon 4 x that entries at most
+// must hold zero; conf gets n*dim, hang n*2dim and hcon 4 x that entries at most.
+// pub (nullable; host memory mapped for the device): the block that finishes last (counted in
+// *done, which must hold zero) copies words[0..nwords) there, then writes seq to pub[nwords], so
+// the host can read the adaptation's counts without a copy and a stream synchronisation.
 struct FaceLists {
   int32_t* conf = nullptr;
   int32_t* hang = nullptr;
   int32_t* hcon = nullptr;
   unsigned long long* count = nullptr;
+  int64_t* pub = nullptr;
+  const int64_t* words = nullptr;
+  int nwords = 0;
+  int64_t seq = 0;
+  unsigned long long* done = nullptr;
 };
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,

@@ -771,6 +771,21 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
       L.hang[h] = int32_t((e << 3) | f);
       for (int r = 0; r < 4; ++r) L.hcon[h * 4 + r] = cv[r];
     }
+    if (L.pub) {
+      // the last block to finish publishes the counts (every block's atomics precede its fence)
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(L.done, 1ull) == gridDim.x - 1ull) {
+          __threadfence();
+          for (int w = 0; w < L.nwords; ++w)
+            L.pub[w] = *reinterpret_cast<const volatile int64_t*>(L.words + w);
+          __threadfence_system();
+          *reinterpret_cast<volatile int64_t*>(L.pub + L.nwords) = L.seq;
+          __threadfence_system();
+        }
+      }
+    }
   }
   if (!fcnt) return;
   if ((f & 1) && type == 0) atomicAdd(&s_cnt[2 * lt], 1);
