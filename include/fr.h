@@ -99,6 +99,9 @@ typedef struct {
   int64_t M_old, M_new;
   int64_t n_refined, n_coarsened; /* leaves flagged and honoured                               */
   int32_t balance_passes;         /* depth passes of the 2:1 balance that split something      */
+  int32_t balance_exact_depth;    /* 0, or the depth of the first balance pass run with exact
+                                     sizes (large meshes; or a pass that generated more octants
+                                     than an adaptation issued without synchronisation holds) */
   double ms_tree, ms_transfer, ms_conn; /* device time of the three parts (Sec. 5.2 breakdown)  */
 } fr_adapt_stats;
 

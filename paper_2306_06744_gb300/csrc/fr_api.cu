@@ -506,21 +506,28 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     }
     return r;
   };
+  int exact_depth = 0;  // the first balance pass run with exact sizes (0: none)
   if (!rc && fast) {
-    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err, &src, &tag);
-    if (!rc) rc = rest(n_ub, ctl + CTL_N);
+    int nslot = CTL_N;  // the slot that holds the balanced tree's leaf count
+    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err, &src, &tag, &nslot);
+    if (!rc) rc = rest(n_ub, ctl + nslot);
+    if (!rc) h_ctl[CTL_N] = h_ctl[nslot];
     if (!rc && h_ctl[CTL_OVER] != 0) {
       // a balance pass generated more octants than the issued passes hold: finish the balance
-      // from that depth with exact sizes and redo the rest
+      // from that depth with exact sizes (from the count in CTL_N) and redo the rest
       const int Dov = int(h_ctl[CTL_OVER]);
-      if (cudaMemsetAsync(ctl + CTL_OVER, 0, 8, s) != cudaSuccess || cudaMemsetAsync(bad, 0, 8, s) != cudaSuccess)
+      if (cudaMemsetAsync(ctl + CTL_OVER, 0, 8, s) != cudaSuccess || cudaMemsetAsync(bad, 0, 8, s) != cudaSuccess ||
+          (nslot != CTL_N &&
+           cudaMemcpyAsync(ctl + CTL_N, ctl + nslot, 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess))
         rc = set_error(err, FR_ECUDA, "memset");
       if (!rc) rc = tree_balance(m->dim, m->g, Dov, Dlow, nk, ctl, n_ub, h_ctl, m->A, s, err);
+      exact_depth = Dov;
       hcon.release(m->A);
       fast = false;
     }
   } else if (!rc) {
     rc = tree_balance(m->dim, m->g, m->g.Dmax, Dlow, nk, ctl, n_ub, h_ctl, m->A, s, err);
+    if (m->g.Dmax >= Dlow && m->g.Dmax >= 2) exact_depth = m->g.Dmax;
   }
   if (!rc && !fast) rc = rest(h_ctl[CTL_N], nullptr);
   if (!rc) rc = conn_check(m, hb);
@@ -582,6 +589,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     st->n_refined = h_ctl[CTL_REF];
     st->n_coarsened = h_ctl[CTL_COARSE];
     st->balance_passes = int(h_ctl[CTL_PASSES]);
+    st->balance_exact_depth = exact_depth;
     st->ms_tree = T.ms(0, 1);
     st->ms_transfer = T.ms(1, 2);
     st->ms_conn = T.ms(2, 3);
@@ -798,6 +806,7 @@ int fr_run(fr_mesh* m, int nsteps, fr_step_stats* sst, fr_adapt_stats* ast) {
       aacc.n_refined += a.n_refined;
       aacc.n_coarsened += a.n_coarsened;
       aacc.balance_passes += a.balance_passes;
+      if (a.balance_exact_depth > aacc.balance_exact_depth) aacc.balance_exact_depth = a.balance_exact_depth;
       aacc.ms_tree += a.ms_tree;
       aacc.ms_transfer += a.ms_transfer;
       aacc.ms_conn += a.ms_conn;

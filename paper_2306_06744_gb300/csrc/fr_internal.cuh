@@ -420,10 +420,12 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys_sorted, int64_t n, Buf
 // [2] refined leaves, [3] coarsened groups, [4] overflowed pass depth (0: none), [5] passes that
 // changed the tree, [6] face-list counts (conforming | hanging << 32); for the merge of a balance
 // pass issued without synchronisation: [7] the leaf count before the pass, [8] the sorted
-// octants it merges; [9] blocks of the connectivity kernel that have finished (FaceLists::pub).
+// octants it merges; [9] blocks of the connectivity kernel that have finished (FaceLists::pub);
+// for balance passes whose merge sorts the octants itself (tree_balance_async): [10], [11] the
+// leaf counts the passes hand on (alternately), [12] the second generated-octant counter.
 enum {
   CTL_N = 0, CTL_G = 1, CTL_REF = 2, CTL_COARSE = 3, CTL_OVER = 4, CTL_PASSES = 5, CTL_FACES = 6,
-  CTL_NPREV = 7, CTL_GS = 8, CTL_DONE = 9, CTL_SLOTS = 10
+  CTL_NPREV = 7, CTL_GS = 8, CTL_DONE = 9, CTL_NA = 10, CTL_NB = 11, CTL_GB = 12, CTL_SLOTS = 13
 };
 // The edit zeroes the control block (and the two error flags d_bad, if given) and leaves its
 // leaf count and statistics there without a host synchronisation; its output holds at most
@@ -442,10 +444,12 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 // generate more sets d_ctl[4] to its depth and leaves the tree unchanged from there on (the caller
 // then finishes with tree_balance from that depth).  With org/otg (those of the edit): carried
 // through the passes, so that they give every leaf of the balanced tree its origin in the tree
-// before the edit and its relation to it, as the old->new mapping (tree_map) would.
+// before the edit and its relation to it, as the old->new mapping (tree_map) would.  *n_slot
+// receives the control-block slot that holds the balanced tree's leaf count (CTL_N, or one of the
+// slots the passes hand the count on in).
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
-                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org = nullptr,
-                       Buf<int8_t>* otg = nullptr);
+                       int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org,
+                       Buf<int8_t>* otg, int* n_slot);
 // d_n_new / d_n (nullable): device leaf count of the new tree; n_new / n is then an upper bound
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
              int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,

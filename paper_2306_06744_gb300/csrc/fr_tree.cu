@@ -386,19 +386,39 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
 constexpr int PACK_BITS = 21;  // leaf indices below 2^21 (meshes of this path hold at most 2^20)
 template <int DIM>
 __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl, int64_t n_ub, KG g,
-                               int D, uint64_t* __restrict__ out, int64_t cap, bool packed) {
+                               int D, uint64_t* __restrict__ out, int64_t cap, bool packed, int sn, int sg) {
   pdl_wait_then_release();
   constexpr int LPL = BalLanes<DIM>::value;
+  constexpr int NC = 1 << DIM;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = gt / LPL;
   const int o = int(gt % LPL);
-  const int64_t n = ctl[CTL_OVER] == 0 ? ctl[CTL_N] : 0;
+  const int64_t n = ctl[CTL_OVER] == 0 ? ctl[sn] : 0;
   uint32_t N[3];
   int dA = 0;
   int64_t jA = 0;
-  const int c = i < n_ub ? bal_lane<DIM>(k, n, g, D, i, o, N, &dA, &jA) : 0;
-  // every lane of the warp takes part: inclusive prefix of the counts, one atomic per warp
+  const bool gen = i < n_ub && bal_lane<DIM>(k, n, g, D, i, o, N, &dA, &jA) > 0;
+  // A lane emits the 2^dim children of its box's ancestor at each depth l-1, l = dA+1 .. D-1.
+  // Lanes of a warp whose boxes share that ancestor (neighbouring leaves looking into the same
+  // coarse leaf) would emit the same octants: per depth only the lowest such lane emits them, so
+  // the set of octants is unchanged and the sort and merge see fewer copies.
   const int lane = int(threadIdx.x & 31);
+  const int l0 = int(__reduce_min_sync(0xffffffffu, unsigned(gen ? dA + 1 : D)));
+  const uint64_t rawN = gen ? interleave<DIM>(N) : 0ull;
+  uint32_t lead = 0;  // bit l - l0: this lane emits depth l's octants
+  int c = 0;
+  for (int l = l0; l <= D - 1; ++l) {
+    const bool act = gen && l > dA;
+    const uint64_t span = vol_raw<DIM>(g, l - 1);
+    // an ancestor key never equals the all-ones value of the lanes that emit nothing
+    const uint64_t anc = act ? g.make(rawN / span * span, l - 1) : ~0ull;
+    const unsigned same = __match_any_sync(0xffffffffu, anc);
+    if (act && lane == __ffs(same) - 1) {
+      lead |= 1u << (l - l0);
+      c += NC;
+    }
+  }
+  // every lane of the warp takes part: inclusive prefix of the counts, one atomic per warp
   int incl = c;
 #pragma unroll
   for (int w = 1; w < 32; w <<= 1) {
@@ -407,15 +427,15 @@ __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restri
   }
   const int tot = __shfl_sync(0xffffffffu, incl, 31);
   unsigned long long base = 0;
-  if (lane == 31 && tot > 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(ctl + CTL_G), (unsigned long long)tot);
+  if (lane == 31 && tot > 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(ctl + sg), (unsigned long long)tot);
   base = __shfl_sync(0xffffffffu, base, 31);
   if (c == 0) return;
   int64_t q = int64_t(base) + (incl - c);
-  const uint64_t rawN = interleave<DIM>(N);
-  for (int l = dA + 1; l <= D - 1; ++l) {
+  for (int l = l0; l <= D - 1; ++l) {
+    if (!((lead >> (l - l0)) & 1u)) continue;
     const uint64_t span = vol_raw<DIM>(g, l - 1);
-    const uint64_t anc = g.make(rawN / span * span, l - 1);  // ancestor of the box at depth l-1
-    for (int ch = 0; ch < (1 << DIM); ++ch, ++q)
+    const uint64_t anc = g.make(rawN / span * span, l - 1);
+    for (int ch = 0; ch < NC; ++ch, ++q)
       if (q < cap) {  // past the capacity: counted, not stored
         const uint64_t ck = child_key<DIM>(g, anc, ch);
         out[q] = packed ? (ck << PACK_BITS) | uint64_t(jA) : ck;
@@ -423,31 +443,12 @@ __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restri
   }
 }
 
-// one block: sorts the pass's octants, computes the merge shifts P[0..nS] and the merged leaf
-// count, and prepares the control block for the merge (CTL_NPREV, CTL_GS) and the next pass
-// (CTL_G zeroed).  An oversized pass, or any pass after one, merges nothing.
-template <int DIM>
-__global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, int64_t* __restrict__ ctl,
-                                                     int64_t cap, int D, const uint64_t* __restrict__ k, KG g,
-                                                     int32_t* __restrict__ P, bool packed) {
-  pdl_wait_then_release();
-  __shared__ uint64_t sk[SMALL_SORT_MAX];
-  __shared__ int32_t wsum[32];
+// Sort of a pass's nS generated values (at most SMALL_SORT_MAX, nS > 0) by one block of 1024
+// threads into sk: a rank sort up to RANK_SORT_MAX values, else a bitonic network over the
+// power-of-two padded array (padding all-ones, sorted last); exchanges closer than 32 elements
+// stay inside one warp and need only a warp barrier.  Ends with a block barrier.
+__device__ __forceinline__ void block_sort_1024(uint64_t* sk, const uint64_t* __restrict__ S, int nS) {
   const int t = threadIdx.x;
-  const int64_t n = ctl[CTL_N];
-  const int64_t G = ctl[CTL_G];
-  const bool over = ctl[CTL_OVER] != 0 || G > cap || G > SMALL_SORT_MAX;
-  __syncthreads();  // every thread has read the control block before thread 0 rewrites it
-  if (over || G == 0) {
-    if (t == 0) {
-      if (ctl[CTL_OVER] == 0 && G > 0) ctl[CTL_OVER] = D;
-      ctl[CTL_NPREV] = n;
-      ctl[CTL_GS] = 0;
-      ctl[CTL_G] = 0;
-    }
-    return;
-  }
-  const int nS = int(G);
   if (nS <= RANK_SORT_MAX) {
     // rank sort: each key's position is the number of smaller keys plus the equal keys before it
     uint64_t mine = 0;
@@ -496,7 +497,35 @@ __global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, i
       }
     }
   }
-  __syncthreads();  // the sorted octants are in sk
+  __syncthreads();
+}
+
+// one block: sorts the pass's octants, computes the merge shifts P[0..nS] and the merged leaf
+// count, and prepares the control block for the merge (CTL_NPREV, CTL_GS) and the next pass
+// (CTL_G zeroed).  An oversized pass, or any pass after one, merges nothing.
+template <int DIM>
+__global__ void __launch_bounds__(1024) k_sort_annot(uint64_t* __restrict__ S, int64_t* __restrict__ ctl,
+                                                     int64_t cap, int D, const uint64_t* __restrict__ k, KG g,
+                                                     int32_t* __restrict__ P, bool packed) {
+  pdl_wait_then_release();
+  __shared__ uint64_t sk[SMALL_SORT_MAX];
+  __shared__ int32_t wsum[32];
+  const int t = threadIdx.x;
+  const int64_t n = ctl[CTL_N];
+  const int64_t G = ctl[CTL_G];
+  const bool over = ctl[CTL_OVER] != 0 || G > cap || G > SMALL_SORT_MAX;
+  __syncthreads();  // every thread has read the control block before thread 0 rewrites it
+  if (over || G == 0) {
+    if (t == 0) {
+      if (ctl[CTL_OVER] == 0 && G > 0) ctl[CTL_OVER] = D;
+      ctl[CTL_NPREV] = n;
+      ctl[CTL_GS] = 0;
+      ctl[CTL_G] = 0;
+    }
+    return;
+  }
+  const int nS = int(G);
+  block_sort_1024(sk, S, nS);  // the sorted octants are in sk
   // per thread 4 consecutive octants r = 4t .. 4t+3: kept(r) - first(r), with first(r) when the
   // containing leaf of r differs from that of r - 1
   // (packed: the containing leaf is the value's low bits, the key its high bits; the sorted keys
@@ -647,6 +676,143 @@ __global__ void k_merge_fast(const uint64_t* __restrict__ k, const int64_t* __re
       }
       ++o;
     }
+}
+
+// lower bound of key v among packed values (key << PACK_BITS | containing leaf), by their keys
+__device__ __forceinline__ int lower_bound_packed(const uint64_t* a, int n, uint64_t v) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((a[mid] >> PACK_BITS) < v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+// A balance pass issued without synchronisation whose octants carry their containing leaf
+// (packed), in two launches instead of three: every block of the merge sorts the pass's octants
+// itself in shared memory and computes the shifts P as k_sort_annot does (the per-leaf merge then
+// follows k_merge_fast), over a grid-stride range of leaves.  The leaf count before the pass is
+// read from slot si and the octant count from slot sg; block 0 writes the merged count to slot so,
+// zeroes slot sg_next (the next pass's octant counter) and records an oversized pass in CTL_OVER
+// (such a pass, and every later one, copies the tree).  No block reads a slot that block 0 writes
+// in the same launch, except CTL_OVER, whose new value leads every block to the same decision.
+template <int DIM>
+__global__ void __launch_bounds__(1024) k_merge_sorted(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl,
+                                                       int64_t n_ub, const uint64_t* __restrict__ S, int64_t cap,
+                                                       int D, int si, int sg, int so, int sg_next, KG g,
+                                                       uint64_t* __restrict__ out, const int32_t* __restrict__ oi,
+                                                       const int8_t* __restrict__ ti, int32_t* __restrict__ oo,
+                                                       int8_t* __restrict__ to) {
+  pdl_wait_then_release();
+  __shared__ uint64_t sk[SMALL_SORT_MAX];
+  __shared__ int16_t sP[SMALL_SORT_MAX + 1];  // |P| <= SMALL_SORT_MAX
+  __shared__ int32_t wsum[32];
+  const int t = threadIdx.x;
+  const int64_t n = ctl[si];
+  const int64_t G = ctl[sg];
+  const bool big = G > cap || G > SMALL_SORT_MAX;
+  const int nS = (ctl[CTL_OVER] != 0 || big) ? 0 : int(G);
+  const int64_t nn = n < n_ub ? n : n_ub;
+  if (blockIdx.x != 0 && int64_t(blockIdx.x) * blockDim.x >= nn) return;  // no leaves here
+  const uint64_t lmask = (1ull << PACK_BITS) - 1;
+  // octant r is kept by the linearisation unless the next one equals it or lies inside it
+  auto keep_of = [&](int r) -> bool {
+    if (r + 1 >= nS) return true;
+    const uint64_t a = sk[r] >> PACK_BITS, b = sk[r + 1] >> PACK_BITS;
+    return !(a == b || is_ancestor<DIM>(g, a, b));
+  };
+  int total = 0;
+  if (nS > 0) {
+    block_sort_1024(sk, S, nS);
+    // per thread 4 consecutive octants r = 4t .. 4t+3: kept(r) - first(r), first(r) when the
+    // containing leaf of r differs from that of r - 1; exclusive block scan into sP
+    int v[4], sum = 0;
+    uint64_t prev_leaf = ~0ull;
+    if (4 * t < nS && 4 * t > 0) prev_leaf = sk[4 * t - 1] & lmask;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = 4 * t + q;
+      v[q] = 0;
+      if (r < nS) {
+        const uint64_t leaf = sk[r] & lmask;
+        v[q] = int(keep_of(r)) - int(leaf != prev_leaf);
+        prev_leaf = leaf;
+      }
+      sum += v[q];
+    }
+    const int lane = t & 31, wid = t >> 5;
+    int incl = sum;
+#pragma unroll
+    for (int w = 1; w < 32; w <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, w);
+      if (lane >= w) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const int x = lane < int(blockDim.x >> 5) ? wsum[lane] : 0;
+      int wi = x;
+#pragma unroll
+      for (int w = 1; w < 32; w <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, wi, w);
+        if (lane >= w) wi += y;
+      }
+      wsum[lane] = wi - x;  // exclusive prefix of the warp totals
+    }
+    __syncthreads();
+    int run = wsum[wid] + incl - sum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = 4 * t + q;
+      if (r < nS) sP[r] = int16_t(run);
+      run += v[q];
+      if (r == nS - 1) sP[nS] = int16_t(run);  // total shift: n + sP[nS] leaves after the merge
+    }
+    __syncthreads();
+    total = sP[nS];
+  }
+  if (blockIdx.x == 0 && t == 0) {
+    if (big && ctl[CTL_OVER] == 0) ctl[CTL_OVER] = D;
+    ctl[so] = n + total;
+    ctl[sg_next] = 0;
+    if (nS > 0) ctl[CTL_PASSES] += 1;
+  }
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + t; i < nn; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t key = k[i];
+    const int32_t src = oo ? oi[i] : 0;
+    const int tag = oo ? ti[i] : 0;
+    int lo = 0, hi = 0;
+    if (nS > 0) {
+      lo = lower_bound_packed(sk, nS, key);
+      hi = lower_bound_packed(sk, nS, key_end<DIM>(g, key));
+    }
+    int64_t o = i + (nS > 0 ? int64_t(sP[lo]) : 0);
+    if (hi == lo) {
+      out[o] = key;
+      if (oo) {
+        oo[o] = src;
+        to[o] = int8_t(tag);
+      }
+      continue;
+    }
+    const int d1 = g.depth(key) + 1;
+    for (int r = lo; r < hi; ++r)
+      if (keep_of(r)) {
+        const uint64_t y = sk[r] >> PACK_BITS;
+        out[o] = y;
+        if (oo) {
+          if (tag == 2) {
+            const uint64_t span = vol_raw<DIM>(g, d1);
+            const int c = child_index<DIM>(g, g.make(g.raw(y) / span * span, d1));
+            oo[o] = src + c;
+            to[o] = int8_t(g.depth(y) == d1 ? 0 : 1);
+          } else {
+            oo[o] = src;
+            to[o] = 1;
+          }
+        }
+        ++o;
+      }
+  }
 }
 
 // Old->new mapping (Sec. 4.2, mapping algorithm) by one lower bound per new leaf.
@@ -1127,36 +1293,66 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
                        int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org,
-                       Buf<int8_t>* otg) {
+                       Buf<int8_t>* otg, int* n_slot) {
   Buf<uint64_t> gen, out;
   Buf<int32_t> org_out;
   Buf<int8_t> otg_out;
   int rc = 0;
   const int64_t cap = SMALL_SORT_MAX;
-  for (int D = g.Dmax; D >= Dlow && D >= 2; --D) {
+  int passes = 0;
+  for (int D = g.Dmax; D >= Dlow && D >= 2; --D) ++passes;
+  // key bits and the containing leaf's index fit one 64-bit value, on every pass: then each
+  // pass's merge sorts the octants itself (k_merge_sorted), otherwise a one-block kernel sorts
+  // them and computes the shifts (k_sort_annot)
+  const bool packed = dim * g.Dmax + g.mb + PACK_BITS <= 64 &&
+                      *n_ub + int64_t(passes) * cap < (int64_t(1) << PACK_BITS);
+  int grid_cap = 0;
+  if (packed) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return set_error(err, FR_ECUDA, "device attribute");
+    grid_cap = 2 * sms;  // two resident 1024-thread blocks per SM: one wave
+  }
+  // leaf-count slots: pass k reads sn and writes the next one (packed: CTL_N -> NB -> NA -> NB ...,
+  // otherwise CTL_N throughout); octant counters alternate between CTL_G and CTL_GB
+  int sn = CTL_N;
+  for (int D = g.Dmax, kp = 0; D >= Dlow && D >= 2; --D, ++kp) {
     Scratch S(&A);
     const int64_t nb = *n_ub;
-    // key bits and the containing leaf's index fit one 64-bit value
-    const bool packed = dim * g.Dmax + g.mb + PACK_BITS <= 64 && nb < (int64_t(1) << PACK_BITS);
-    int32_t* P = S.get<int32_t>(cap + 1);
-    if (!P || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap)) ||
+    const int sg = (packed && (kp & 1)) ? CTL_GB : CTL_G;
+    int32_t* P = packed ? nullptr : S.get<int32_t>(cap + 1);
+    if ((!packed && !P) || gen.ensure(A, size_t(cap)) || out.ensure(A, size_t(nb + cap)) ||
         (org && (org_out.ensure(A, size_t(nb + cap)) || otg_out.ensure(A, size_t(nb + cap))))) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
     DIM_DISPATCH(dim, (launch_dependent(k_bal_gen_fast<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g,
-                                        D, gen.p, cap, packed)));
+                                        D, gen.p, cap, packed, sn, sg)));
     ++launch_counter();
-    DIM_DISPATCH(dim, (launch_dependent(k_sort_annot<D_>, 1, 1024, s, gen.p, d_ctl, cap, D,
-                                        static_cast<const uint64_t*>(keys.p), g, P, packed)));
-    ++launch_counter();
-    DIM_DISPATCH(dim, (launch_dependent(k_merge_fast<D_>, nblk(nb), TB, s, static_cast<const uint64_t*>(keys.p),
-                                        static_cast<const int64_t*>(d_ctl), nb, static_cast<const uint64_t*>(gen.p),
-                                        static_cast<const int32_t*>(P), g, out.p,
-                                        static_cast<const int32_t*>(org ? org->p : nullptr),
-                                        static_cast<const int8_t*>(org ? otg->p : nullptr),
-                                        org ? org_out.p : nullptr, org ? otg_out.p : nullptr)));
-    ++launch_counter();
+    if (packed) {
+      const int so = (kp & 1) ? CTL_NA : CTL_NB;
+      const int sg_next = (kp & 1) ? CTL_G : CTL_GB;
+      int64_t grid = nblk(nb, 1024);
+      if (grid > grid_cap) grid = grid_cap;
+      DIM_DISPATCH(dim, (launch_dependent(k_merge_sorted<D_>, unsigned(grid), 1024, s, static_cast<const uint64_t*>(keys.p),
+                                          d_ctl, nb, static_cast<const uint64_t*>(gen.p), cap, D, sn, sg, so,
+                                          sg_next, g, out.p, static_cast<const int32_t*>(org ? org->p : nullptr),
+                                          static_cast<const int8_t*>(org ? otg->p : nullptr),
+                                          org ? org_out.p : nullptr, org ? otg_out.p : nullptr)));
+      ++launch_counter();
+      sn = so;
+    } else {
+      DIM_DISPATCH(dim, (launch_dependent(k_sort_annot<D_>, 1, 1024, s, gen.p, d_ctl, cap, D,
+                                          static_cast<const uint64_t*>(keys.p), g, P, packed)));
+      ++launch_counter();
+      DIM_DISPATCH(dim, (launch_dependent(k_merge_fast<D_>, nblk(nb), TB, s, static_cast<const uint64_t*>(keys.p),
+                                          static_cast<const int64_t*>(d_ctl), nb, static_cast<const uint64_t*>(gen.p),
+                                          static_cast<const int32_t*>(P), g, out.p,
+                                          static_cast<const int32_t*>(org ? org->p : nullptr),
+                                          static_cast<const int8_t*>(org ? otg->p : nullptr),
+                                          org ? org_out.p : nullptr, org ? otg_out.p : nullptr)));
+      ++launch_counter();
+    }
     if (cudaGetLastError() != cudaSuccess) {
       rc = set_error(err, FR_ECUDA, "balance pass launch");
       break;
@@ -1170,6 +1366,7 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
     }
     *n_ub = nb + cap;
   }
+  *n_slot = sn;
   gen.release(A);
   out.release(A);
   org_out.release(A);

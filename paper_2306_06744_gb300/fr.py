@@ -41,6 +41,7 @@ class FRNorms(C.Structure):
 class FRAdaptStats(C.Structure):
     _fields_ = [("M_old", C.c_int64), ("M_new", C.c_int64), ("n_refined", C.c_int64),
                 ("n_coarsened", C.c_int64), ("balance_passes", C.c_int32),
+                ("balance_exact_depth", C.c_int32),
                 ("ms_tree", C.c_double), ("ms_transfer", C.c_double), ("ms_conn", C.c_double)]
 
 

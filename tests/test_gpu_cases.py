@@ -114,13 +114,14 @@ def test_extreme_degrees(p):
 
 
 def test_balance_pass_beyond_octant_capacity():
-    # Left half of the periodic square at depth 8, right half at depth 7 (balanced); refining every
-    # depth-8 leaf puts depth-9 leaves against depth-7 ones along both interfaces, so one balance
-    # pass generates ~1.2e4 octants: more than an adaptation issued without host synchronisation
-    # holds per pass (4096), which then finishes that pass and the rest with exact sizes.
+    # Sixteen stripes across the periodic square, alternately at depth 8 and depth 7 (balanced);
+    # refining every depth-8 leaf puts depth-9 leaves against depth-7 ones along all sixteen
+    # interfaces, so the first balance pass must split 16 x 128 depth-7 leaves into 8192 distinct
+    # octants: more than an adaptation issued without host synchronisation holds per pass (4096),
+    # which then finishes that pass and the rest with exact sizes.
     cfg = _cfg("vortex2d_p2_small", Dbase=6, Dmax=9)
-    boxes = [(8, x, y, 0) for x in range(0, 256, 2) for y in range(0, 512, 2)]
-    boxes += [(7, x, y, 0) for x in range(256, 512, 4) for y in range(0, 512, 4)]
+    boxes = [(8, x, y, 0) for a in range(8) for x in range(64 * a, 64 * a + 32, 2) for y in range(0, 512, 2)]
+    boxes += [(7, x, y, 0) for a in range(8) for x in range(64 * a + 32, 64 * a + 64, 4) for y in range(0, 512, 4)]
     keys = np.sort(O.morton_encode(2, 9, np.array(boxes)))
     g = fr.Mesh(cfg)
     o = O.OracleMesh(cfg)
@@ -131,6 +132,7 @@ def test_balance_pass_beyond_octant_capacity():
     flags = np.where(depth == 8, 1, 0).astype(np.int8)
     st = g.adapt(flags, stats=True)
     o.adapt(flags)
+    assert st["balance_exact_depth"] == 9  # the first pass overflowed and ran with exact sizes
     assert np.array_equal(g.leaves(), o.leaves())
     assert st["M_new"] == len(o.leaves()) and st["n_refined"] == 32768
     assert rel_l2(g.state(), o.state()) < 1e-13
@@ -151,8 +153,9 @@ def test_full_size_2d_p3_workload():
         o.step(10)
         assert rel_l2(g.state(), o.state()) < 1e-10
         fo, _ = o.flags()
-        g.adapt(fo)
+        st = g.adapt(fo, stats=True)
         o.adapt(fo)
+        assert st["balance_exact_depth"] == 0  # issued without synchronisation, as timed
         assert np.array_equal(g.leaves(), o.leaves())
         assert rel_l2(g.state(), o.state()) < 1e-10
     ng, no = g.norms(), o.norms()
