@@ -132,8 +132,10 @@ int check_cfg(const fr_config* c, Err* err) {
 // lists are written in leaf order after a scan of the per-leaf counts.
 // seq > 0 (append only): the kernel also publishes the mesh's ctlblk words to its mapped host words
 // with this sequence number.
+// X (append only): a sampled index of keys for the searches (tab null: none).
 static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int64_t* d_n, int64_t* d_faces,
-                      int32_t* bad, Buf<int32_t>& hcon, bool append = false, int64_t seq = 0) {
+                      int32_t* bad, Buf<int32_t>& hcon, bool append = false, int64_t seq = 0,
+                      const KeyIndex& X = KeyIndex{}) {
   Err* err = &m->err;
   cudaStream_t s = m->stream;
   const int64_t S = n_ub * m->nfc;
@@ -151,6 +153,7 @@ static int conn_issue(fr_mesh* m, const uint64_t* keys, int64_t n_ub, const int6
     L.hang = m->hang.p;
     L.hcon = hcon.p;
     L.count = reinterpret_cast<unsigned long long*>(d_faces);
+    L.index = X;
     if (seq > 0 && m->pub_d) {
       L.pub = m->pub_d;
       L.words = m->ctlblk.p;
@@ -441,6 +444,11 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<int32_t> src, hcon;
   Buf<int8_t> tag, retr;
   Buf<double> ntr;
+  // sampled indexes of the edited and balanced trees (issued without synchronisation): the edit
+  // writes the first, each balance pass the next, and the searches of the passes and of the
+  // connectivity read them
+  Buf<uint64_t> tabA, tabB;
+  KeyIndex X;
   bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
   // the traces of unchanged elements are carried over by the transfer (when the current ones are
   // valid); only refined and fused elements get theirs computed afterwards
@@ -448,8 +456,22 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   // issued without synchronisation, the edit and the balance passes carry each new leaf's origin
   // in the old tree (src) and its relation to it (tag): the old->new mapping of Sec. 4.2 without a
   // search
+  if (fast) {
+    int passes = 0;
+    for (int D = m->g.Dmax; D >= Dlow && D >= 2; --D) ++passes;
+    X.sh = key_index_shift(n_ub + int64_t(passes) * 4096);
+    const size_t nt = size_t(((n_ub + int64_t(passes) * 4096) >> X.sh) + 1);
+    int r0 = tabA.ensure(m->A, nt);
+    if (!r0) r0 = tabB.ensure(m->A, nt);
+    if (r0) {  // nothing of the mesh has changed yet
+      tabA.release(m->A);
+      tabB.release(m->A);
+      return r0;
+    }
+    X.tab = tabA.p;
+  }
   int rc = tree_edit(m->dim, m->g, m->cfg.Dbase, m->keys.p, fl, M0, nk, ctl, bad, m->A, s, err,
-                     fast ? &src : nullptr, fast ? &tag : nullptr);
+                     fast ? &src : nullptr, fast ? &tag : nullptr, X);
   // map, transfer and connectivity of the new tree nk (leaf count *d_n, at most nb)
   auto rest = [&](int64_t nb, const int64_t* d_n) -> int {
     int r = 0;
@@ -482,7 +504,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       // issued without synchronisation: the edit's first kernel zeroed the face counter and the
       // finished-block counter; the last block publishes the counts to mapped host memory
       seq = (fast && m->pub_h) ? ++m->pub_seq : 0;
-      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast, seq);
+      r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast, seq, fast ? X : KeyIndex{});
     }
     // the traces of the refined and fused elements (the others were carried), before the
     // synchronisation, against the device leaf count
@@ -509,7 +531,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   int exact_depth = 0;  // the first balance pass run with exact sizes (0: none)
   if (!rc && fast) {
     int nslot = CTL_N;  // the slot that holds the balanced tree's leaf count
-    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err, &src, &tag, &nslot);
+    rc = tree_balance_async(m->dim, m->g, Dlow, nk, ctl, &n_ub, m->A, s, err, &src, &tag, &nslot, &X,
+                            X.tab ? tabB.p : nullptr);
     if (!rc) rc = rest(n_ub, ctl + nslot);
     if (!rc) h_ctl[CTL_N] = h_ctl[nslot];
     if (!rc && h_ctl[CTL_OVER] != 0) {
@@ -534,6 +557,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   const int64_t M1 = h_ctl[CTL_N];
   src.release(m->A);
   tag.release(m->A);
+  tabA.release(m->A);
+  tabB.release(m->A);
   if (!rc) {
     // the time-step buffers for the new size, while the mesh still holds the old tree (a block
     // that is released and not replaced here is grown again by ready_buffers)

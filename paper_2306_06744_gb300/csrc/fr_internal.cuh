@@ -247,6 +247,58 @@ __device__ __forceinline__ int64_t upper_bound_dev(const uint64_t* a, int64_t n,
   return lo;
 }
 
+// Sampled index of a sorted key array k[0..n): tab[j] = k[j << sh] for j < ceil(n / 2^sh),
+// written by the kernel that writes k (KeyIndex::note at every output position).  A search first
+// bisects the samples, staged in shared memory, then the 2^sh keys between two samples: on a tree
+// of 20k leaves and sh = 7 that is about 4 dependent global reads instead of 15.
+constexpr int KEY_INDEX_MAX = 1024;  // samples per index (8 KB of shared memory)
+struct KeyIndex {
+  uint64_t* tab = nullptr;  // null: no index (a plain binary search)
+  int sh = 0;
+  __device__ __forceinline__ void note(int64_t o, uint64_t key) const {
+    if (tab && (o & ((int64_t(1) << sh) - 1)) == 0) tab[o >> sh] = key;
+  }
+};
+// the smallest sampling shift >= 7 that keeps an index of n_ub keys within KEY_INDEX_MAX samples
+inline int key_index_shift(int64_t n_ub) {
+  int sh = 7;
+  while (((n_ub + (int64_t(1) << sh) - 1) >> sh) > KEY_INDEX_MAX) ++sh;
+  return sh;
+}
+// Block-wide (every thread calls it): stages the samples of an index of n keys in s_tab and
+// returns their count (0 without an index).  Ends with a block barrier.
+__device__ __forceinline__ int stage_key_index(const KeyIndex& X, int64_t n, uint64_t* s_tab) {
+  const int m = X.tab ? int((n + (int64_t(1) << X.sh) - 1) >> X.sh) : 0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) s_tab[j] = X.tab[j];
+  __syncthreads();
+  return m;
+}
+// first index in k[0..n) with k[i] > v (upper) or >= v (lower), using m staged samples
+// (m = 0: plain binary search)
+template <bool UPPER>
+__device__ __forceinline__ int64_t bound_indexed(const uint64_t* k, int64_t n, uint64_t v, const uint64_t* s_tab,
+                                                 int m, int sh) {
+  int64_t a = 0, b = n;
+  if (m > 0) {
+    int lo = 0, hi = m;  // first sample past v
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (UPPER ? (s_tab[mid] <= v) : (s_tab[mid] < v)) lo = mid + 1; else hi = mid;
+    }
+    if (lo == 0) return 0;  // k[0] is the first sample
+    // k[(lo-1) << sh] is before the bound, and k[lo << sh] (if any) is past it
+    a = (int64_t(lo - 1) << sh) + 1;
+    b = int64_t(lo) << sh;
+    if (b > n) b = n;
+  }
+  while (a < b) {
+    const int64_t mid = (a + b) >> 1;
+    const uint64_t x = __ldg(k + mid);
+    if (UPPER ? (x <= v) : (x < v)) a = mid + 1; else b = mid;
+  }
+  return a;
+}
+
 // Old->new mapping of one new leaf (Sec. 4.2, mapping algorithm) by one lower bound in the old
 // keys: tag 0 copy of old leaf *src, 1 refined from old leaf *src, 2 fused from the 2^dim old
 // leaves starting at *src.  A new leaf that is none of these makes the tree pair invalid: *bad is
@@ -433,7 +485,8 @@ enum {
 // it (0 the same leaf, 1 inside it, 2 the parent of the 2^dim old leaves from the origin on).
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
               int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
-              Err* err, Buf<int32_t>* org = nullptr, Buf<int8_t>* otg = nullptr);
+              Err* err, Buf<int32_t>* org = nullptr, Buf<int8_t>* otg = nullptr,
+              const KeyIndex& XO = KeyIndex{});
 // balances `keys` in place for depth passes D = Dhigh .. Dlow with exact sizes (one host
 // synchronisation per pass); the leaf count is d_ctl[0] on entry (at most n_ub) and h_ctl
 // (CTL_SLOTS values) holds the final control block on return
@@ -447,9 +500,12 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 // before the edit and its relation to it, as the old->new mapping (tree_map) would.  *n_slot
 // receives the control-block slot that holds the balanced tree's leaf count (CTL_N, or one of the
 // slots the passes hand the count on in).
+// X (in/out): the index of keys (tab null: none), carried through the passes that sort their
+// octants themselves, with spare_tab (as large as X's table) as the other buffer; on return the
+// index of the balanced tree, or none.
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
                        int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org,
-                       Buf<int8_t>* otg, int* n_slot);
+                       Buf<int8_t>* otg, int* n_slot, KeyIndex* X, uint64_t* spare_tab);
 // d_n_new / d_n (nullable): device leaf count of the new tree; n_new / n is then an upper bound
 int tree_map(int dim, const KG& g, const uint64_t* d_old, int64_t n_old, const uint64_t* d_new,
              int64_t n_new, const int64_t* d_n_new, int32_t* d_src, int8_t* d_tag, int32_t* d_bad,
@@ -474,6 +530,7 @@ struct FaceLists {
   int nwords = 0;
   int64_t seq = 0;
   unsigned long long* done = nullptr;
+  KeyIndex index;  // of the keys (nullable): the searches use it
 };
 int tree_conn(int dim, const KG& g, const uint64_t* d_keys, int64_t n, const int64_t* d_n, int32_t* d_nbr,
               int8_t* d_ftype, int8_t* d_slot, int32_t* d_contrib, int32_t* d_bad, cudaStream_t s,

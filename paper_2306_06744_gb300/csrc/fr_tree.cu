@@ -64,6 +64,29 @@ __global__ void k_compact(const uint64_t* __restrict__ k, const int32_t* __restr
 // (becomes the parent), 3 other member of that group (removed).  Coarsening needs all 2^dim
 // siblings present as consecutive leaves (raw IDs consecutive, Sec. 4.1) and all flagged -1.
 template <int DIM>
+__device__ __forceinline__ int edit_action(const uint64_t* __restrict__ k, const int8_t* __restrict__ flags,
+                                           int64_t n, const KG& g, int Dbase, int64_t i) {
+  constexpr int NC = 1 << DIM;
+  const uint64_t key = k[i];
+  const int d = g.depth(key);
+  const int f = flags[i];
+  if (f > 0 && d < g.Dmax) return 1;
+  if (f < 0 && d > Dbase) {
+    const int c = child_index<DIM>(g, key);
+    const int64_t h = i - c;
+    bool ok = h >= 0 && h + NC <= n;
+    if (ok) {
+      const uint64_t par = parent_key<DIM>(g, key);
+      for (int s = 0; s < NC && ok; ++s)
+        ok = k[h + s] == child_key<DIM>(g, par, s) && flags[h + s] < 0;
+    }
+    if (ok) return (c == 0) ? 2 : 3;
+  }
+  return 0;
+}
+__device__ __forceinline__ int edit_count(int a, int dim) { return a == 1 ? (1 << dim) : (a == 3 ? 0 : 1); }
+
+template <int DIM>
 __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __restrict__ flags,
                              int64_t n, KG g, int Dbase, int8_t* __restrict__ act,
                              int32_t* __restrict__ cnt, int64_t* __restrict__ ctl,
@@ -75,32 +98,75 @@ __global__ void k_edit_count(const uint64_t* __restrict__ k, const int8_t* __res
     if (flags_out) flags_out[0] = flags_out[1] = 0;
   }
   if (i >= n) return;
-  constexpr int NC = 1 << DIM;
-  uint64_t key = k[i];
-  int d = g.depth(key);
-  int f = flags[i];
-  int a = 0;
-  if (f > 0 && d < g.Dmax) {
-    a = 1;
-  } else if (f < 0 && d > Dbase) {
-    int c = child_index<DIM>(g, key);
-    int64_t h = i - c;
-    bool ok = h >= 0 && h + NC <= n;
-    if (ok) {
-      uint64_t par = parent_key<DIM>(g, key);
-      for (int s = 0; s < NC && ok; ++s)
-        ok = k[h + s] == child_key<DIM>(g, par, s) && flags[h + s] < 0;
-    }
-    if (ok) a = (c == 0) ? 2 : 3;
-  }
+  const int a = edit_action<DIM>(k, flags, n, g, Dbase, i);
   act[i] = int8_t(a);
-  cnt[i] = a == 1 ? NC : (a == 3 ? 0 : 1);
+  cnt[i] = edit_count(a, DIM);
+}
+
+// The edit's actions and output counts with the tile-local exclusive scan of the counts in one
+// launch: a block of 256 threads takes one tile of SCAN_TILE_ITEMS leaves (8 consecutive leaves
+// per thread), writes each leaf's offset inside the tile and the tile's total to sums[block];
+// k_edit_write adds the tile's base (offs_base).  Zeroes the control block like k_edit_count.
+constexpr int EDIT_SCAN_T = 256, EDIT_SCAN_I = int(SCAN_TILE_ITEMS) / EDIT_SCAN_T;
+template <int DIM>
+__global__ void __launch_bounds__(EDIT_SCAN_T) k_edit_scan(const uint64_t* __restrict__ k,
+                                                          const int8_t* __restrict__ flags, int64_t n, KG g,
+                                                          int Dbase, int8_t* __restrict__ act,
+                                                          int64_t* __restrict__ offs, int64_t* __restrict__ sums,
+                                                          int64_t* __restrict__ ctl, int32_t* __restrict__ flags_out) {
+  pdl_wait_then_release();
+  __shared__ int32_t s_warp[EDIT_SCAN_T / 32];
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  if (blockIdx.x == 0 && t == 0) {  // the adaptation's control block and error flags start at zero
+    for (int c = 0; c < CTL_SLOTS; ++c) ctl[c] = 0;
+    if (flags_out) flags_out[0] = flags_out[1] = 0;
+  }
+  const int64_t i0 = int64_t(blockIdx.x) * SCAN_TILE_ITEMS + int64_t(t) * EDIT_SCAN_I;
+  int c[EDIT_SCAN_I], run = 0;
+#pragma unroll
+  for (int q = 0; q < EDIT_SCAN_I; ++q) {
+    const int64_t i = i0 + q;
+    c[q] = 0;
+    if (i < n) {
+      const int a = edit_action<DIM>(k, flags, n, g, Dbase, i);
+      act[i] = int8_t(a);
+      c[q] = edit_count(a, DIM);
+    }
+    run += c[q];
+  }
+  int incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) s_warp[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < EDIT_SCAN_T / 32 ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < EDIT_SCAN_T / 32) s_warp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  int64_t o = int64_t(incl - run + (wid ? s_warp[wid - 1] : 0));
+#pragma unroll
+  for (int q = 0; q < EDIT_SCAN_I; ++q) {
+    const int64_t i = i0 + q;
+    if (i < n) offs[i] = o;
+    o += c[q];
+  }
+  if (t == EDIT_SCAN_T - 1) sums[blockIdx.x] = s_warp[EDIT_SCAN_T / 32 - 1];
 }
 
 template <int DIM>
 __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __restrict__ act,
                              const Offs O, int64_t n, KG g, uint64_t* __restrict__ out,
-                             unsigned long long* stats, int32_t* __restrict__ org, int8_t* __restrict__ otg) {
+                             unsigned long long* stats, int32_t* __restrict__ org, int8_t* __restrict__ otg,
+                             const KeyIndex XO) {
   pdl_wait_then_release();
   int64_t grand;
   const int64_t base = offs_base(O, int64_t(blockIdx.x) * blockDim.x, &grand);
@@ -110,15 +176,25 @@ __global__ void k_edit_write(const uint64_t* __restrict__ k, const int8_t* __res
   int64_t o = O.offs[i] + base;
   const int a = act[i];
   switch (a) {
-    case 0: out[o] = key; break;
+    case 0:
+      out[o] = key;
+      XO.note(o, key);
+      break;
     case 1:
-      for (int c = 0; c < (1 << DIM); ++c) out[o + c] = child_key<DIM>(g, key, c);
+      for (int c = 0; c < (1 << DIM); ++c) {
+        const uint64_t ck = child_key<DIM>(g, key, c);
+        out[o + c] = ck;
+        XO.note(o + c, ck);
+      }
       atomicAdd(&stats[0], 1ull);
       break;
-    case 2:
-      out[o] = parent_key<DIM>(g, key);
+    case 2: {
+      const uint64_t pk = parent_key<DIM>(g, key);
+      out[o] = pk;
+      XO.note(o, pk);
       atomicAdd(&stats[1], 1ull);
       break;
+    }
     default: break;
   }
   if (org && a != 3) {
@@ -142,7 +218,8 @@ struct Nofs {
 
 template <int DIM>
 __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_t n, const KG& g,
-                                          int D, int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr) {
+                                          int D, int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr,
+                                          const uint64_t* s_tab = nullptr, int m = 0, int sh = 0) {
   uint64_t key = k[i];
   if (g.depth(key) != D) return false;
   int oo = o < (DIM == 2 ? 4 : 13) ? o : o + 1;  // skip the centre of the 3^dim stencil
@@ -153,7 +230,7 @@ __device__ __forceinline__ bool bal_query(const uint64_t* __restrict__ k, int64_
     int off = (oo / (a == 0 ? 1 : (a == 1 ? 3 : 9))) % 3 - 1;
     N[a] = (x[a] + uint32_t(off) * w) & mask;  // periodic wrap on the 2^Dmax grid
   }
-  int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
+  int64_t j = bound_indexed<true>(k, n, cell_key<DIM>(g, N), s_tab, m, sh) - 1;
   if (j < 0) j = 0;  // only on an incomplete tree, which callers reject beforehand
   *dA = g.depth(k[j]);
   if (jA) *jA = j;
@@ -183,10 +260,11 @@ struct BalLanes {
 // number of octants lane (i, o) generates, with the containing leaf's depth and the box
 template <int DIM>
 __device__ __forceinline__ int bal_lane(const uint64_t* __restrict__ k, int64_t n, const KG& g, int D,
-                                        int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr) {
+                                        int64_t i, int o, uint32_t* N, int* dA, int64_t* jA = nullptr,
+                                        const uint64_t* s_tab = nullptr, int m = 0, int sh = 0) {
   constexpr int NO = Nofs<DIM>::value;
   if (i >= n || o >= NO) return 0;
-  return bal_query<DIM>(k, n, g, D, i, o, N, dA, jA) ? (D - 1 - *dA) << DIM : 0;
+  return bal_query<DIM>(k, n, g, D, i, o, N, dA, jA, s_tab, m, sh) ? (D - 1 - *dA) << DIM : 0;
 }
 
 template <int DIM>
@@ -386,18 +464,24 @@ __global__ void k_merge_write(const uint64_t* __restrict__ k, const int64_t* __r
 constexpr int PACK_BITS = 21;  // leaf indices below 2^21 (meshes of this path hold at most 2^20)
 template <int DIM>
 __global__ void k_bal_gen_fast(const uint64_t* __restrict__ k, int64_t* __restrict__ ctl, int64_t n_ub, KG g,
-                               int D, uint64_t* __restrict__ out, int64_t cap, bool packed, int sn, int sg) {
+                               int D, uint64_t* __restrict__ out, int64_t cap, bool packed, int sn, int sg,
+                               const KeyIndex X) {
   pdl_wait_then_release();
+  __shared__ uint64_t s_tab[KEY_INDEX_MAX];
   constexpr int LPL = BalLanes<DIM>::value;
   constexpr int NC = 1 << DIM;
   const int64_t gt = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t i = gt / LPL;
   const int o = int(gt % LPL);
   const int64_t n = ctl[CTL_OVER] == 0 ? ctl[sn] : 0;
+  // the key index is staged only by blocks that hold a depth-D leaf (the others search nothing)
+  const bool deep = i < n_ub && i < n && g.depth(k[i]) == D;
+  int m = 0;
+  if (__syncthreads_or(deep)) m = stage_key_index(X, n, s_tab);
   uint32_t N[3];
   int dA = 0;
   int64_t jA = 0;
-  const bool gen = i < n_ub && bal_lane<DIM>(k, n, g, D, i, o, N, &dA, &jA) > 0;
+  const bool gen = deep && bal_lane<DIM>(k, n, g, D, i, o, N, &dA, &jA, s_tab, m, X.sh) > 0;
   // A lane emits the 2^dim children of its box's ancestor at each depth l-1, l = dA+1 .. D-1.
   // Lanes of a warp whose boxes share that ancestor (neighbouring leaves looking into the same
   // coarse leaf) would emit the same octants: per depth only the lowest such lane emits them, so
@@ -701,7 +785,7 @@ __global__ void __launch_bounds__(1024) k_merge_sorted(const uint64_t* __restric
                                                        int D, int si, int sg, int so, int sg_next, KG g,
                                                        uint64_t* __restrict__ out, const int32_t* __restrict__ oi,
                                                        const int8_t* __restrict__ ti, int32_t* __restrict__ oo,
-                                                       int8_t* __restrict__ to) {
+                                                       int8_t* __restrict__ to, const KeyIndex XO) {
   pdl_wait_then_release();
   __shared__ uint64_t sk[SMALL_SORT_MAX];
   __shared__ int16_t sP[SMALL_SORT_MAX + 1];  // |P| <= SMALL_SORT_MAX
@@ -788,6 +872,7 @@ __global__ void __launch_bounds__(1024) k_merge_sorted(const uint64_t* __restric
     int64_t o = i + (nS > 0 ? int64_t(sP[lo]) : 0);
     if (hi == lo) {
       out[o] = key;
+      XO.note(o, key);
       if (oo) {
         oo[o] = src;
         to[o] = int8_t(tag);
@@ -799,6 +884,7 @@ __global__ void __launch_bounds__(1024) k_merge_sorted(const uint64_t* __restric
       if (keep_of(r)) {
         const uint64_t y = sk[r] >> PACK_BITS;
         out[o] = y;
+        XO.note(o, y);
         if (oo) {
           if (tag == 2) {
             const uint64_t span = vol_raw<DIM>(g, d1);
@@ -838,8 +924,12 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
   // leaf's face-list counts, conforming faces it owns (its + faces) low, coarse sides of hanging
   // faces high; leaves past the count get zero
   __shared__ int s_cnt[2 * 256 / NFC + 2];
+  __shared__ uint64_t s_tab[KEY_INDEX_MAX];
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int64_t n = d_n ? *d_n : n_ub;
+  // blocks past the leaf count (the grid is sized by a bound of it) search nothing
+  const int m = int64_t(blockIdx.x) * blockDim.x < n * NFC ? stage_key_index(L.index, n, s_tab) : 0;
+  const int sh = L.index.sh;
   const int lt = int(threadIdx.x) / NFC;
   if (fcnt && int(threadIdx.x) % NFC == 0) s_cnt[2 * lt] = s_cnt[2 * lt + 1] = 0;
   if (fcnt) __syncthreads();
@@ -858,7 +948,7 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
     for (int a = 0; a < DIM; ++a) N[a] = x[a];
     N[axis] = (x[axis] + (side ? w : (0u - w))) & mask;
     const uint64_t kN = g.make(interleave<DIM>(N), d);
-    int64_t j = upper_bound_dev(k, n, cell_key<DIM>(g, N)) - 1;
+    int64_t j = bound_indexed<true>(k, n, cell_key<DIM>(g, N), s_tab, m, sh) - 1;
     if (j < 0) j = 0;
     const uint64_t kj = k[j];
     const int dj = g.depth(kj);
@@ -885,16 +975,16 @@ __global__ void k_conn(const uint64_t* __restrict__ k, int64_t n_ub, const int64
       for (int c = 0; c < (1 << DIM); ++c) {
         if (((c >> axis) & 1) != (side ? 0 : 1)) continue;
         uint64_t kc = child_key<DIM>(g, kN, c);
-        int64_t m = lower_bound_dev(k, n, kc);
-        if (m >= n || k[m] != kc) {
+        int64_t q = bound_indexed<false>(k, n, kc, s_tab, m, sh);
+        if (q >= n || k[q] != kc) {
           atomicExch(bad, 1);
-          m = 0;
+          q = 0;
         }
-        int sl = 0, sh = 0;
+        int sl = 0, sb = 0;
         for (int b = 0; b < DIM; ++b)
-          if (b != axis) sl |= ((c >> b) & 1) << sh++;
-        if (sl == 0) first = int(m);
-        cv[sl] = int32_t(m);
+          if (b != axis) sl |= ((c >> b) & 1) << sb++;
+        if (sl == 0) first = int(q);
+        cv[sl] = int32_t(q);
       }
       if (contrib)
         for (int r = 0; r < 4; ++r) contrib[t * 4 + r] = cv[r];
@@ -1157,9 +1247,12 @@ int tree_linearise(int dim, const KG& g, uint64_t* d_keys, int64_t n, Buf<uint64
   return 0;
 }
 
+// the write kernel adds up to this many tile totals per block (offs_base)
+constexpr int64_t EDIT_SCAN_TILES_MAX = 256;
+
 int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int8_t* d_flags,
               int64_t n, Buf<uint64_t>& out, int64_t* d_ctl, int32_t* d_bad, Alloc& A, cudaStream_t s,
-              Err* err, Buf<int32_t>* org, Buf<int8_t>* otg) {
+              Err* err, Buf<int32_t>* org, Buf<int8_t>* otg, const KeyIndex& XO) {
   Scratch S(&A);
   int8_t* act = S.get<int8_t>(n);
   int32_t* cnt = S.get<int32_t>(n);
@@ -1168,18 +1261,29 @@ int tree_edit(int dim, const KG& g, int Dbase, const uint64_t* d_keys, const int
   // the edited tree has at most 2^dim leaves per old leaf: the output is sized for that bound and
   // the leaf count stays on the device for the balance passes
   FR_TRY(out.ensure(A, size_t(n) << dim));
-  DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt,
-                                      d_ctl, d_bad)));
-  FR_LAUNCH_CHECK(err);
   Offs O;
-  FR_TRY(scan_counts_local(cnt, offs, n, d_ctl + CTL_N, S, s, err, &O));
+  const int64_t tiles = (n + SCAN_TILE_ITEMS - 1) / SCAN_TILE_ITEMS;
+  if (tiles <= EDIT_SCAN_TILES_MAX) {
+    // actions, counts and the tile-local scan in one launch; the write adds the tile bases
+    int64_t* sums = S.get<int64_t>(tiles);
+    if (!sums) return set_error(err, FR_ENOMEM, "edit scratch");
+    DIM_DISPATCH(dim, (launch_dependent(k_edit_scan<D_>, unsigned(tiles), EDIT_SCAN_T, s, d_keys, d_flags, n, g, Dbase,
+                                        act, offs, sums, d_ctl, d_bad)));
+    FR_LAUNCH_CHECK(err);
+    O = Offs{offs, sums, tiles, d_ctl + CTL_N};
+  } else {
+    DIM_DISPATCH(dim, (launch_dependent(k_edit_count<D_>, nblk(n), TB, s, d_keys, d_flags, n, g, Dbase, act, cnt,
+                                        d_ctl, d_bad)));
+    FR_LAUNCH_CHECK(err);
+    FR_TRY(scan_counts_local(cnt, offs, n, d_ctl + CTL_N, S, s, err, &O));
+  }
   if (org) {
     FR_TRY(org->ensure(A, size_t(n) << dim));
     FR_TRY(otg->ensure(A, size_t(n) << dim));
   }
   DIM_DISPATCH(dim, (launch_dependent(k_edit_write<D_>, nblk(n), TB, s, d_keys, act, O, n, g, out.p,
                                       reinterpret_cast<unsigned long long*>(d_ctl + CTL_REF),
-                                      org ? org->p : nullptr, org ? otg->p : nullptr)));
+                                      org ? org->p : nullptr, org ? otg->p : nullptr, XO)));
   FR_LAUNCH_CHECK(err);
   return 0;
 }
@@ -1293,7 +1397,7 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
 
 int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int64_t* d_ctl,
                        int64_t* n_ub, Alloc& A, cudaStream_t s, Err* err, Buf<int32_t>* org,
-                       Buf<int8_t>* otg, int* n_slot) {
+                       Buf<int8_t>* otg, int* n_slot, KeyIndex* X, uint64_t* spare_tab) {
   Buf<uint64_t> gen, out;
   Buf<int32_t> org_out;
   Buf<int8_t> otg_out;
@@ -1306,6 +1410,8 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
   // them and computes the shifts (k_sort_annot)
   const bool packed = dim * g.Dmax + g.mb + PACK_BITS <= 64 &&
                       *n_ub + int64_t(passes) * cap < (int64_t(1) << PACK_BITS);
+  // the key index travels with the tree only through passes that write it (k_merge_sorted)
+  if (!packed || !spare_tab) X->tab = nullptr;
   int grid_cap = 0;
   if (packed) {
     int dev = 0, sms = 0;
@@ -1327,7 +1433,7 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
       break;
     }
     DIM_DISPATCH(dim, (launch_dependent(k_bal_gen_fast<D_>, nblk(nb * BalLanes<D_>::value), TB, s, keys.p, d_ctl, nb, g,
-                                        D, gen.p, cap, packed, sn, sg)));
+                                        D, gen.p, cap, packed, sn, sg, *X)));
     ++launch_counter();
     if (packed) {
       const int so = (kp & 1) ? CTL_NA : CTL_NB;
@@ -1338,9 +1444,11 @@ int tree_balance_async(int dim, const KG& g, int Dlow, Buf<uint64_t>& keys, int6
                                           d_ctl, nb, static_cast<const uint64_t*>(gen.p), cap, D, sn, sg, so,
                                           sg_next, g, out.p, static_cast<const int32_t*>(org ? org->p : nullptr),
                                           static_cast<const int8_t*>(org ? otg->p : nullptr),
-                                          org ? org_out.p : nullptr, org ? otg_out.p : nullptr)));
+                                          org ? org_out.p : nullptr, org ? otg_out.p : nullptr,
+                                          KeyIndex{X->tab ? spare_tab : nullptr, X->sh})));
       ++launch_counter();
       sn = so;
+      if (X->tab) std::swap(X->tab, spare_tab);
     } else {
       DIM_DISPATCH(dim, (launch_dependent(k_sort_annot<D_>, 1, 1024, s, gen.p, d_ctl, cap, D,
                                           static_cast<const uint64_t*>(keys.p), g, P, packed)));
