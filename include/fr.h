@@ -145,9 +145,10 @@ int fr_run(fr_mesh* m, int nsteps, fr_step_stats* step_stats, fr_adapt_stats* ad
    Sec. 4.2, connectivity Sec. 3.3).  flags: device int8[M] in {-1,0,1} borrowed for the call, or
    NULL to evaluate the configured indicator.  Refinement at Dmax and coarsening at Dbase are
    ignored; a leaf changes at most one level before balancing.  stats may be NULL.  The whole
-   adaptation is issued against device-side counts with one host synchronisation at its end when
-   2^dim * M <= 2^20 (a balance pass generating more than 4096 octants is then finished with exact
-   sizes, one synchronisation per pass); larger meshes synchronise once per balance pass.
+   adaptation is issued against device-side counts when 2^dim * M <= 2^20, and the call waits once,
+   at its end, for the counts the device publishes to mapped host memory (a balance pass
+   generating more than 4096 octants is then finished with exact sizes, one synchronisation per
+   pass); larger meshes synchronise once per balance pass.
    FR_EINVAL if the new tree fails a consistency check; FR_ETIMEOUT from the learned indicator. */
 int fr_adapt(fr_mesh* m, const int8_t* dev_flags, fr_adapt_stats* stats);
 
