@@ -491,7 +491,8 @@ def main():
         uout = torch.empty(cap * nv * N, dtype=torch.float64).pin_memory().numpy()
         keys_h = None
         dof_e, t_e, bi, bo = 0, 0.0, 0, 0
-        for k in range(args.e2e_steps + 1):
+        e2e_warm = 2  # untimed passes: the first DMA transfers from fresh pinned buffers can be slow
+        for k in range(args.e2e_steps + e2e_warm):
             if mesh.M > cap:  # the inputs must fit the pinned buffers: grow them (untimed)
                 cap = mesh.M + mesh.M // 4 + 1024
                 kin = torch.empty(cap, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
@@ -512,15 +513,16 @@ def main():
             k2 = mesh.leaves(out=kout if fits else None)
             u2 = mesh.state(out=uout if fits else None)
             b = time.perf_counter()
-            if k == 0:
-                continue  # first pass warms the pinned-buffer path
+            if k < e2e_warm:
+                continue
             dof_e += ae * M0 * N * nv
             t_e += b - a
             bi += kn.nbytes + un_.nbytes
             bo += k2.nbytes + u2.nbytes
         dof_e, t_e = aggregate_ranks(dof_e, t_e)
         e2e = {"value": dof_e / t_e, "unit": UNIT,
-               "h2d_bytes_per_step": bi // args.e2e_steps, "d2h_bytes_per_step": bo // args.e2e_steps}
+               "h2d_bytes_per_step": bi // args.e2e_steps, "d2h_bytes_per_step": bo // args.e2e_steps,
+               "steps": args.e2e_steps, "warmup": e2e_warm}
         del keys_h
 
     # the other arithmetic forms of the time-step kernels on the same workload and cycles:
