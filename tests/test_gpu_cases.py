@@ -113,6 +113,28 @@ def test_extreme_degrees(p):
     assert rel_l2(g.state(), o.state()) < 1e-10
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tiny_mesh_random_adaptations(dim):
+    # base level 1 (2^dim leaves) up to level 3: random flags refine and fuse around the whole
+    # periodic box, so the adaptation issued without synchronisation meets its smallest trees,
+    # refinement clamped at Dmax and fusion clamped at the base level
+    cfg = _cfg("vortex2d_p2_small", dim=dim, p=2, Dbase=1, Dmax=3)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    for k in range(6):
+        g.step(1)
+        o.step(1)
+        flags = W.random_flags(o.M, 70 + k, p_refine=0.4, p_coarsen=0.5)
+        st = g.adapt(flags, stats=True)
+        o.adapt(flags)
+        assert st["balance_exact_depth"] == 0
+        assert np.array_equal(g.leaves(), o.leaves())
+        assert rel_l2(g.state(), o.state()) < 1e-10
+        for a, b in zip(g.conn(), O.conn(dim, 3, o.leaves())):
+            assert np.array_equal(a, b)
+
+
 def test_balance_pass_beyond_octant_capacity():
     # Sixteen stripes across the periodic square, alternately at depth 8 and depth 7 (balanced);
     # refining every depth-8 leaf puts depth-9 leaves against depth-7 ones along all sixteen

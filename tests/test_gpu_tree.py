@@ -77,6 +77,28 @@ def test_adapt_map_conn(dim, Dbase, Dmax, seed):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_degenerate_trees(dim):
+    # the root alone (its own neighbour through every periodic face) and the 2^dim leaves of
+    # depth 1: balance, connectivity, fusing every leaf back into the root and refining the root
+    Dmax = 4
+    root = O.morton_encode(dim, Dmax, np.array([[0, 0, 0, 0]]))
+    kids = np.sort(O.morton_encode(dim, Dmax, np.array(
+        [[1, (c & 1) * 8, ((c >> 1) & 1) * 8, ((c >> 2) & 1) * 8 if dim == 3 else 0] for c in range(1 << dim)])))
+    for keys in (root, kids):
+        assert np.array_equal(fr.tree_balance(dim, Dmax, keys), O.balance(dim, Dmax, keys))
+        for a, b in zip(fr.tree_conn(dim, Dmax, keys), O.conn(dim, Dmax, keys)):
+            assert np.array_equal(a, b)
+    for keys, flag, Dbase in ((kids, -1, 0), (root, 1, 0), (kids, -1, 1), (kids, 1, 1)):
+        flags = np.full(len(keys), flag, dtype=np.int8)
+        want = O.adapt_keys(dim, Dbase, Dmax, keys, flags)
+        got = fr.tree_adapt(dim, Dbase, Dmax, keys, flags)
+        assert np.array_equal(got, want)
+        s_o, t_o = O.map_trees(dim, Dmax, keys, want)
+        s_g, t_g = fr.tree_map(dim, Dmax, keys, got)
+        assert np.array_equal(s_g, s_o) and np.array_equal(t_g, t_o)
+
+
 def test_conn_rejects_unbalanced():
     dim, Dmax = 2, 5
     boxes = [(1, 16, 0, 0), (1, 0, 16, 0), (1, 16, 16, 0)]
