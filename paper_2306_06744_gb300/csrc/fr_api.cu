@@ -337,6 +337,7 @@ int stage(fr_mesh* m, const double* us, const double* un, double* out, double a,
   S.a = a;
   S.b = b;
   S.c = c;
+  S.rk = rk_mode(a, b);
   S.status = m->status;
   S.flags = flags;
   S.th_r = m->cfg.th_refine;

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_s
     const int64_t b0 = (e0 + le) * EU + i;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-      unr[v] = A.a != 0.0 ? A.un[b0 + v * N] : 0.0;
+      unr[v] = (A.rk & RK_A) ? A.un[b0 + v * N] : 0.0;
       su[le * EU + v * N + i] = Ar<T>::from_d(A.us[b0 + v * N]);
     }
   }
@@ -484,14 +484,14 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_s
       // FP64 combination (native FP64 and the mixed FP32 form).  The first stage (a = 0, b = 1)
       // is one FMA per value; the branch is uniform over the grid (kernel arguments), so the
       // other stages do not pay for it
-      if (A.a == 0.0 && A.b == 1.0) {
+      if (A.rk == RK_B1) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) outv[v] = fma(cs, Ar<T>::to_d(R[v]), usr[v]);
       } else {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-          double o = fma(cs, Ar<T>::to_d(R[v]), A.b == 1.0 ? usr[v] : A.b * usr[v]);
-          if (A.a != 0.0) o = fma(A.a, unr[v], o);
+          double o = fma(cs, Ar<T>::to_d(R[v]), (A.rk & RK_B1) ? usr[v] : A.b * usr[v]);
+          if (A.rk & RK_A) o = fma(A.a, unr[v], o);
           outv[v] = o;
         }
       }
@@ -501,7 +501,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_s
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         ff o = fma_t(bb, su[le * EU + v * N + i], cc * R[v]);
-        if (A.a != 0.0) o = fma_t(aa, ff_from_double(unr[v]), o);
+        if (A.rk & RK_A) o = fma_t(aa, ff_from_double(unr[v]), o);
         outv[v] = o;
       }
     }

@@ -25,10 +25,14 @@ struct StageArgs {
   int64_t M;
   KG g;
   double twoL, gamma, a, b, c;  // twoL = 2 / L
+  int rk;                       // RK_A: a != 0; RK_B1: b == 1 (integer tests, no FP64 compares per thread)
   int* status;                  // device word set by a tensor-core kernel whose completion wait gave up
   int8_t* flags;                // FP64 form: density-gradient flags of out (nullable)
   double th_r, th_c;            // their refine / coarsen thresholds
 };
+
+enum { RK_A = 1, RK_B1 = 2 };
+inline int rk_mode(double a, double b) { return (a != 0.0 ? RK_A : 0) | (b == 1.0 ? RK_B1 : 0); }
 
 struct Mesh;  // defined in fr_api.cu
 

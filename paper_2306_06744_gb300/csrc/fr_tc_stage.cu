@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(TS_T) k_stage_tc(StageArgs A, const __grid_con
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
       const double us = A.us[base + v * TS_N];
-      double o = fma(cs, Ar<float>::to_d(R[v]), A.b == 1.0 ? us : A.b * us);
-      if (A.a != 0.0) o = fma(A.a, A.un[base + v * TS_N], o);
+      double o = fma(cs, Ar<float>::to_d(R[v]), (A.rk & RK_B1) ? us : A.b * us);
+      if (A.rk & RK_A) o = fma(A.a, A.un[base + v * TS_N], o);
       A.out[base + v * TS_N] = o;
       su[e * TS_EU + v * TS_N + i] = Ar<float>::from_d(o);
     }
