@@ -23,6 +23,9 @@ struct OpsT {
   T gLh[NPMAX], gRh[NPMAX], lm[NPMAX], lp[NPMAX];
   T I[2][NPMAX][NPMAX];
   T P[2][NPMAX][NPMAX];
+  // gas constants in the arithmetic type, formed on the host (set_gas): gamma, gamma - 1 and
+  // -(gamma - 1)/2, so that no thread spends FP64 operations on them
+  T gam, gm1, ngmh;
 };
 
 inline double host_conv(double x, double*) { return x; }
@@ -31,6 +34,14 @@ inline ff host_conv(double x, ff*) {
   float h = float(x);
   float l = float(x - double(h));
   return ff{h, l};
+}
+
+template <class T>
+void set_gas(OpsT<T>* r, double gamma) {
+  T* tag = nullptr;
+  r->gam = host_conv(gamma, tag);
+  r->gm1 = host_conv(gamma - 1.0, tag);
+  r->ngmh = host_conv(-0.5 * (gamma - 1.0), tag);
 }
 
 template <class T>
@@ -139,21 +150,6 @@ __device__ __forceinline__ void rusanov2_t(const T* qL, const T* qR, int axis, T
   for (int v = 0; v < NV; ++v) F2[v] = fma_t(lam, qL[v] - qR[v], fL[v] + fR[v]);
 }
 
-template <class T>
-__device__ __forceinline__ T cst(double x);
-template <>
-__device__ __forceinline__ double cst<double>(double x) {
-  return x;
-}
-template <>
-__device__ __forceinline__ float cst<float>(double x) {
-  return float(x);
-}
-template <>
-__device__ __forceinline__ ff cst<ff>(double x) {
-  return ff_from_double(x);
-}
-
 // traces tr[e][f][v][q] = sum_j l_j(+-1) u[e][v][line point j]  (mortar procedure step 1).
 // Blocks of EPB elements as in the element kernel: the elements' state is staged in shared memory
 // with coalesced loads, then one thread per (element, face, face point) forms all variables.
@@ -236,7 +232,7 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   __shared__ T sF[FPB][NSUB][NV][NF];
   const T* trace = static_cast<const T*>(A.trace);
   T* fcomm = static_cast<T*>(A.fcomm);
-  const T gam = cst<T>(A.gamma), gm1 = cst<T>(A.gamma - 1.0), ngmh = cst<T>(-0.5 * (A.gamma - 1.0));
+  const T gam = ops.gam, gm1 = ops.gm1, ngmh = ops.ngmh;
   const int tid = threadIdx.x;
   // the face lists and neighbour tables are fixed during a time step: they are read while the
   // element kernel this one depends on drains; the traces it wrote are read after the wait
@@ -407,7 +403,7 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_s
     sg2[tid] = 0ull;
   }
   __syncthreads();
-  const T gm1 = cst<T>(A.gamma - 1.0), ngmh = cst<T>(-0.5 * (A.gamma - 1.0));
+  const T gm1 = ops.gm1, ngmh = ops.ngmh;
   RT outv[NV];
   if (act) {
     const T* q = su + le * EU;
@@ -613,6 +609,7 @@ template <class T>
 int launch_faces_impl(int dim, int p, FaceArgs A, const DevOps& o, cudaStream_t s, Err* err) {
   if (A.n_conf + A.n_hang == 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
+  set_gas(&ops, A.gamma);
   FR_NP_DISPATCH(dim, p, ({
                    using FC = FaceCfg<DD, NN>;
                    const int NF = DD == 2 ? NN : NN * NN;
@@ -645,6 +642,7 @@ template <class T>
 int launch_stage_impl(int dim, int p, const StageArgs& A, const DevOps& o, cudaStream_t s, Err* err) {
   if (A.M <= 0) return 0;
   OpsT<T> ops = make_ops_t<T>(o);
+  set_gas(&ops, A.gamma);
   FR_NP_DISPATCH(dim, p, ({
                    using SS = Sz<DD, NN>;
                    unsigned nb = unsigned((A.M + SS::EPB - 1) / SS::EPB);

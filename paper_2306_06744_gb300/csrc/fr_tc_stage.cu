@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(TS_T) k_stage_tc(StageArgs A, const __grid_con
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t e0 = int64_t(blockIdx.x) * TS_E;
   const int ne = int((A.M - e0) < TS_E ? (A.M - e0) : TS_E);
-  const float gm1 = float(A.gamma - 1.0), ngmh = float(-0.5 * (A.gamma - 1.0));
+  const float gm1 = ops.gm1, ngmh = ops.ngmh;
   if (tid == 0) tc::mbar_init(mb, 1);
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(sm + OFF_BAR + 8), TS_TMEM_COLS);
   // B operands (prepared on the host in their shared-memory layout)
@@ -384,7 +384,8 @@ int launch_tc(const StageArgs& A, const DevOps& o, cudaStream_t s, Err* err) {
     FR_CUDA(err, cudaFuncSetAttribute(k_stage_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr = true;
   }
-  const OpsT<float> ops = make_ops_t<float>(o);
+  OpsT<float> ops = make_ops_t<float>(o);
+  set_gas(&ops, A.gamma);
   const TcB tb = make_tc_b(KIND, o);
   const unsigned nb = unsigned((A.M + TS_E - 1) / TS_E);
   if (launch_dependent_smem(k_stage_tc<KIND>, nb, TS_T, size_t(SMEM_BYTES), s, A, ops, tb) != cudaSuccess)
