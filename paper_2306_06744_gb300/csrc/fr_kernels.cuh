@@ -230,6 +230,9 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   constexpr int PER = FaceCfg<DIM, NP>::PER, BT = FaceCfg<DIM, NP>::T;
   constexpr int FPB = FaceCfg<DIM, NP>::FPB;
   __shared__ T sF[FPB][NSUB][NV][NF];
+  // 3D: the sum-factorised mortar stages' partial sums (interpolation HA, back-projection HB)
+  constexpr int HA = 2 * NV * NP * NP, HB = NSUB * NV * NP * NP;
+  __shared__ T sW[FPB][DIM == 3 ? (HA > HB ? HA : HB) : 1];
   const T* trace = static_cast<const T*>(A.trace);
   T* fcomm = static_cast<T*>(A.fcomm);
   const T gam = ops.gam, gm1 = ops.gm1, ngmh = ops.ngmh;
@@ -277,12 +280,25 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
     ek = A.contrib[hf * 4 + s];
   }
   pdl_wait_then_release();
+  const T* tc = trace + ((ec * NFC + fc) * NV) * NF;
+  const int q0 = q % NP, h0 = s & 1;
+  if (DIM == 3) {
+    // the coarse trace's interpolation to the mortar pieces, sum-factorised across the face's
+    // threads: first along the face's first axis for both halves, a1[h0][v][q0][j1], shared
+    if (act)
+      for (int k = r; k < HA; k += PER) {
+        const int j1 = k % NP, qa = (k / NP) % NP, v = (k / (NP * NP)) % NV, ha = k / (NP * NP * NV);
+        T a1 = zero_t<T>();
+#pragma unroll
+        for (int j0 = 0; j0 < NP; ++j0) a1 = fma_t(ops.I[ha][qa][j0], tc[v * NF + j0 + NP * j1], a1);
+        sW[lf][k] = a1;
+      }
+    __syncthreads();
+  }
   if (act) {
     int axis = fc >> 1, sidec = fc & 1;
     int fk = fc ^ 1;
-    const T* tc = trace + ((ec * NFC + fc) * NV) * NF;
     T uc[NV], uf[NV], F[NV];
-    const int q0 = q % NP, h0 = s & 1;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       T acc = zero_t<T>();
@@ -290,14 +306,12 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
 #pragma unroll
         for (int j0 = 0; j0 < NP; ++j0) acc = fma_t(ops.I[h0][q0][j0], tc[v * NF + j0], acc);
       } else {
+        // then along the second axis, per thread (the same operations in the same order as the
+        // direct tensor-product sum)
         const int q1 = q / NP, h1 = s >> 1;
+        const T* a1 = &sW[lf][((h0 * NV + v) * NP + q0) * NP];
 #pragma unroll
-        for (int j1 = 0; j1 < NP; ++j1) {
-          T a1 = zero_t<T>();
-#pragma unroll
-          for (int j0 = 0; j0 < NP; ++j0) a1 = fma_t(ops.I[h0][q0][j0], tc[v * NF + j0 + NP * j1], a1);
-          acc = fma_t(ops.I[h1][q1][j1], a1, acc);
-        }
+        for (int j1 = 0; j1 < NP; ++j1) acc = fma_t(ops.I[h1][q1][j1], a1[j1], acc);
       }
       uc[v] = acc;
       uf[v] = trace[((ek * NFC + fk) * NV + v) * NF + q];
@@ -314,26 +328,34 @@ __global__ void __launch_bounds__(FaceCfg<DIM, NP>::T) k_faces_t(FaceArgs A, con
   }
   __syncthreads();
   // back-projection onto the coarse face: its NV*NF outputs are spread over all PER threads of
-  // the face (an idle lane costs the FP64 unit as much as a busy one)
+  // the face (an idle lane costs the FP64 unit as much as a busy one); in 3D sum-factorised
+  // across the threads, first along the first axis per mortar piece, b1[sp][v][q0][i1] (reusing
+  // the interpolation's shared buffer), then each output along the second axis
+  if (DIM == 3) {
+    if (act)
+      for (int k = r; k < HB; k += PER) {
+        const int i1 = k % NP, qa = (k / NP) % NP, v = (k / (NP * NP)) % NV, sp = k / (NP * NP * NV);
+        T b1 = zero_t<T>();
+#pragma unroll
+        for (int i0 = 0; i0 < NP; ++i0) b1 = fma_t(ops.P[sp & 1][qa][i0], sF[lf][sp][v][i0 + NP * i1], b1);
+        sW[lf][k] = b1;
+      }
+    __syncthreads();
+  }
   if (act) {
     for (int o = r; o < NV * NF; o += PER) {
-      const int v = o / NF, qc = o % NF, q0 = qc % NP;
+      const int v = o / NF, qc = o % NF, qo = qc % NP;
       T acc = zero_t<T>();
 #pragma unroll
       for (int sp = 0; sp < NSUB; ++sp) {
-        const int h0 = sp & 1;
         if (DIM == 2) {
 #pragma unroll
-          for (int i0 = 0; i0 < NP; ++i0) acc = fma_t(ops.P[h0][q0][i0], sF[lf][sp][v][i0], acc);
+          for (int i0 = 0; i0 < NP; ++i0) acc = fma_t(ops.P[sp & 1][qo][i0], sF[lf][sp][v][i0], acc);
         } else {
           const int q1 = qc / NP, h1 = sp >> 1;
+          const T* b1 = &sW[lf][((sp * NV + v) * NP + qo) * NP];
 #pragma unroll
-          for (int i1 = 0; i1 < NP; ++i1) {
-            T a1 = zero_t<T>();
-#pragma unroll
-            for (int i0 = 0; i0 < NP; ++i0) a1 = fma_t(ops.P[h0][q0][i0], sF[lf][sp][v][i0 + NP * i1], a1);
-            acc = fma_t(ops.P[h1][q1][i1], a1, acc);
-          }
+          for (int i1 = 0; i1 < NP; ++i1) acc = fma_t(ops.P[h1][q1][i1], b1[i1], acc);
         }
       }
       fcomm[((ec * NFC + fc) * NV + v) * NF + qc] = acc;
