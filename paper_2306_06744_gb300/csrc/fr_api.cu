@@ -443,7 +443,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   Buf<uint64_t> nk;
   Buf<double> nu;
   Buf<int32_t> src, hcon;
-  Buf<int8_t> tag, retr;
+  Buf<int8_t> tag;
   Buf<double> ntr;
   // sampled indexes of the edited and balanced trees (issued without synchronisation): the edit
   // writes the first, each balance pass the next, and the searches of the passes and of the
@@ -489,8 +489,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       TraceCopy tc{};
       if (!r && carry) {
         r = ntr.ensure(m->A, size_t(nb) * m->EF);
-        if (!r) r = retr.ensure(m->A, size_t(nb));
-        tc = TraceCopy{m->trace.p, ntr.p, retr.p, m->EF * trace_elem_bytes(m->cfg.precision)};
+        tc = TraceCopy{m->trace.p, ntr.p, trace_kind(m->cfg.precision), m->EF * trace_elem_bytes(m->cfg.precision)};
       }
       if (!r)
         r = launch_transfer(m->dim, m->p, m->g, m->keys.p, M0, nk.p, src.p, tag.p, bad + 1, nb, d_n, m->ops, m->u.p,
@@ -507,10 +506,6 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
       seq = (fast && m->pub_h) ? ++m->pub_seq : 0;
       r = conn_issue(m, nk.p, nb, d_n, ctl + CTL_FACES, bad, hcon, fast, seq, fast ? X : KeyIndex{});
     }
-    // the traces of the refined and fused elements (the others were carried), before the
-    // synchronisation, against the device leaf count
-    if (!r && carry)
-      r = launch_traces(m->cfg.precision, m->dim, m->p, nu.p, nb, m->ops, ntr.p, s, err, retr.p, d_n);
     // one read: the control block, the error flags and the status word are adjacent
     if (!r && seq > 0) {
       r = wait_published(m, seq, h_ctl);
@@ -577,7 +572,6 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
     nu.release(m->A);
     hcon.release(m->A);
     ntr.release(m->A);
-    retr.release(m->A);
     if (conn_dirty) {
       Err keep = *err;
       rebuild_conn(m);
@@ -604,9 +598,8 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   m->flags_fresh = false;
   rc = conn_finish(m, h_ctl[CTL_FACES], hb, hcon);
   hcon.release(m->A);
-  if (!rc && carry) m->traces_ok = true;  // computed before the synchronisation
+  if (!rc && carry) m->traces_ok = true;  // carried or computed by the transfer
   if (!rc && transfer && !carry) rc = refresh_traces(m);
-  retr.release(m->A);
   FR_TRY(rc);
   T.mark(3);
   if (st) {

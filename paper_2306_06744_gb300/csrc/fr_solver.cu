@@ -311,7 +311,6 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_transfer(KG g, const uint64
       for (int k = i; k < w; k += N) b[k] = a[k];
     }
   }
-  if (act && i == 0 && tc.retrace) tc.retrace[j] = int8_t(tg != 0);
   // rounds of the contraction: 1 for a refined element, 2^dim (one per child) for a fused one
   if (act && i == 0 && tg != 0) atomicMax(&s_rounds, tg == 1 ? 1 : (1 << DIM));
   if (act && tg == 1) {
@@ -376,6 +375,36 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT) k_transfer(KG g, const uint64
   if (work) {
 #pragma unroll
     for (int v = 0; v < NV; ++v) un[(j * NV + v) * N + i] = acc[v];
+  }
+  if (tc.dst && rounds > 0) {
+    // the traces of this block's refined and fused elements, from their new state staged in
+    // shared memory (the last round ended with a barrier): one thread per (element, face, face
+    // point), all variables, the same sums in the same order as the trace kernel in FP64
+    constexpr int NF = S::NF, FQ = S::NFC * NF, EF = S::EF;
+    if (work) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sa[le][v * N + i] = acc[v];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < EPB * FQ; k += blockDim.x) {
+      const int le2 = k / FQ, r = k % FQ;
+      if (j0 + le2 >= Mn || s_tag[le2] == 0) continue;
+      const int f = r / NF, q = r % NF;
+      const double* lf = (f & 1) ? ops.lp : ops.lm;
+      const int64_t o = (j0 + le2) * EF + f * NV * NF + q;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double t = 0.0;
+#pragma unroll
+        for (int m = 0; m < NP; ++m) t = fma(lf[m], sa[le2][v * N + line_pt<DIM, NP>(f >> 1, q, m)], t);
+        if (tc.kind == 0)
+          static_cast<double*>(tc.dst)[o + v * NF] = t;
+        else if (tc.kind == 1)
+          static_cast<float*>(tc.dst)[o + v * NF] = __double2float_rn(t);
+        else
+          static_cast<ff*>(tc.dst)[o + v * NF] = ff_from_double(t);
+      }
+    }
   }
 }
 

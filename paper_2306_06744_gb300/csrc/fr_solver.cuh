@@ -69,14 +69,17 @@ int launch_indicator(int dim, int p, int mode, double th_r, double th_c, double 
                      const DevOps& ops, const double* u, int8_t* flags, double* eta,
                      cudaStream_t s, Err* err);
 // Traces carried over by the transfer (all null: none): an unchanged element's `bytes` of traces
-// are copied from src (old elements) to dst (new elements), and retrace[j] says whether new
-// element j needs its traces computed.
+// are copied from src (old elements) to dst (new elements); a refined or fused element's traces
+// are computed from its new state (FP64 sums in the trace kernel's order) and stored in the
+// arithmetic type `kind` of the traces (0 FP64, 1 FP32, 2 double-word).
 struct TraceCopy {
   const void* src;
   void* dst;
-  int8_t* retrace;
+  int kind;
   int bytes;
 };
+// the trace storage kind of a precision form (see TraceCopy)
+inline int trace_kind(int prec) { return prec == 0 ? 0 : (prec == 4 ? 2 : 1); }
 // d_M_new (nullable): device count of new leaves, M_new then an upper bound.  src/tag: the
 // old->new mapping, or null: the kernel maps the new leaves itself (mapping failures set *bad)
 int launch_transfer(int dim, int p, const KG& g, const uint64_t* old_keys, int64_t n_old, const uint64_t* new_keys,
