@@ -1303,14 +1303,16 @@ static int read_ctl(const int64_t* d_ctl, int64_t* h_ctl, cudaStream_t s, Err* e
 static int balance_pass(int dim, const KG& g, int D, Buf<uint64_t>& keys, Buf<uint64_t>& out,
                         Buf<uint64_t>& gen, Buf<uint64_t>& tmp, int64_t* d_ctl, int64_t n_ub,
                         int64_t exact_G, int64_t cap, const Offs& Ocnt, Alloc& A, cudaStream_t s,
-                        Err* err) {
+                        Err* err, bool generated = false) {
   Scratch S(&A);
   const int64_t G_ub = exact_G >= 0 ? exact_G : cap;
-  FR_TRY(gen.ensure(A, size_t(G_ub)));
   FR_TRY(out.ensure(A, size_t(n_ub + G_ub)));
-  DIM_DISPATCH(dim, (launch_dependent(k_bal_gen<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D,
-                                      Ocnt, gen.p, cap)));
-  FR_LAUNCH_CHECK(err);
+  if (!generated) {  // otherwise gen already holds the pass's exact_G octants
+    FR_TRY(gen.ensure(A, size_t(G_ub)));
+    DIM_DISPATCH(dim, (launch_dependent(k_bal_gen<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D,
+                                        Ocnt, gen.p, cap)));
+    FR_LAUNCH_CHECK(err);
+  }
   if (exact_G < 0 || exact_G <= SMALL_SORT_MAX) {
     launch_dependent(k_sort_small, 1, 1024, s, gen.p, d_ctl, cap, D);
     FR_LAUNCH_CHECK(err);
@@ -1361,30 +1363,50 @@ int tree_balance(int dim, const KG& g, int Dhigh, int Dlow, Buf<uint64_t>& keys,
   bool known = false;  // h_ctl holds the current control block
   for (int D = Dhigh; D >= Dlow && D >= 2; --D) {
     if (!known && n_ub > BAL_UB_MAX) {
-      // large trees: counting and scanning up to a loose bound costs more than a synchronisation
+      // large trees: generating up to a loose bound costs more than a synchronisation
       if ((rc = read_ctl(d_ctl, h_ctl, s, err))) break;
       n_ub = h_ctl[CTL_N];
     }
     Scratch S(&A);
-    int32_t* cnt = S.get<int32_t>(n_ub);
-    int64_t* offs = S.get<int64_t>(n_ub);
-    if (!cnt || !offs) {
+    // one search pass: the octants are placed by an atomic counter (sorted next, so their order
+    // does not matter) into room for max(2^16, 2n) of them; a pass that generates more is counted,
+    // scanned and generated again at exact positions
+    const int64_t capG = 2 * n_ub > (int64_t(1) << 16) ? 2 * n_ub : (int64_t(1) << 16);
+    if (gen.ensure(A, size_t(capG)) || cudaMemsetAsync(d_ctl + CTL_G, 0, 8, s) != cudaSuccess) {
       rc = set_error(err, FR_ENOMEM, "balance scratch");
       break;
     }
-    DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n_ub, g, D, cnt)));
+    DIM_DISPATCH(dim, (launch_dependent(k_bal_gen_fast<D_>, nblk(n_ub * BalLanes<D_>::value), TB, s, keys.p, d_ctl,
+                                        n_ub, g, D, gen.p, capG, false, int(CTL_N), int(CTL_G), KeyIndex{})));
     ++launch_counter();
-    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
-    if ((rc = scan_counts(cnt, offs, n_ub, d_ctl + CTL_G, S, s, err))) break;
+    if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_gen_fast") : 0)) break;
     // the pass's one synchronisation: leaf count, generated count (and the edit's statistics)
     if ((rc = read_ctl(d_ctl, h_ctl, s, err))) break;
     known = true;
-    const int64_t n = h_ctl[CTL_N], G = h_ctl[CTL_G];
+    const int64_t n = h_ctl[CTL_N];
+    int64_t G = h_ctl[CTL_G];
     n_ub = n;
     if (G == 0) continue;
-    if ((rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, Offs{offs, nullptr, 0, d_ctl + CTL_G},
-                           A, s, err)))
-      break;
+    if (G <= capG) {
+      rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, Offs{}, A, s, err, true);
+    } else {
+      // the exact count (every lane's octants, duplicates included) sizes the regeneration
+      int32_t* cnt = S.get<int32_t>(n);
+      int64_t* offs = S.get<int64_t>(n);
+      if (!cnt || !offs) {
+        rc = set_error(err, FR_ENOMEM, "balance scratch");
+        break;
+      }
+      DIM_DISPATCH(dim, (launch_dependent(k_bal_count<D_>, nblk(n * BalLanes<D_>::value), TB, s, keys.p, d_ctl, n, g, D, cnt)));
+      ++launch_counter();
+      if ((rc = cudaGetLastError() != cudaSuccess ? set_error(err, FR_ECUDA, "k_bal_count") : 0)) break;
+      if ((rc = scan_counts(cnt, offs, n, d_ctl + CTL_G, S, s, err))) break;
+      if ((rc = read_ctl(d_ctl, h_ctl, s, err))) break;
+      G = h_ctl[CTL_G];
+      rc = balance_pass(dim, g, D, keys, out, gen, tmp, d_ctl, n, G, G, Offs{offs, nullptr, 0, d_ctl + CTL_G}, A, s,
+                        err);
+    }
+    if (rc) break;
     n_ub = n + G;
     known = false;
   }
