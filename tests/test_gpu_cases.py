@@ -135,6 +135,24 @@ def test_tiny_mesh_random_adaptations(dim):
             assert np.array_equal(a, b)
 
 
+def test_deep_octree_adaptations_unpacked_keys():
+    # Dmax 14 in 3D: a key and a leaf index no longer share 64 bits, so the balance passes issued
+    # without synchronisation take their three-kernel form (one-block sort of plain keys)
+    cfg = _cfg("vortex3d_p2_tube", Dbase=2, Dmax=14, init_passes=0)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    assert np.array_equal(g.leaves(), o.leaves())
+    for k in range(5):
+        flags = W.random_flags(o.M, 90 + k, p_refine=0.15, p_coarsen=0.3)
+        st = g.adapt(flags, stats=True)
+        o.adapt(flags)
+        if k < 3:  # small trees: no pass outgrows the unsynchronised passes' 4096 octants
+            assert st["balance_exact_depth"] == 0
+        assert np.array_equal(g.leaves(), o.leaves())
+        assert rel_l2(g.state(), o.state()) < 1e-12
+    assert o.M > 64
+
+
 def test_balance_pass_beyond_octant_capacity():
     # Sixteen stripes across the periodic square, alternately at depth 8 and depth 7 (balanced);
     # refining every depth-8 leaf puts depth-9 leaves against depth-7 ones along all sixteen
