@@ -81,6 +81,25 @@ __device__ __forceinline__ ff fabs_t(ff a) { return a.h < 0.f ? -a : a; }
 __device__ __forceinline__ bool lt_t(ff a, ff b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
 __device__ __forceinline__ ff fmax_t(ff a, ff b) { return lt_t(a, b) ? b : a; }
 
+// Dot-product accumulator for double-word operands (the compensated dot product of Ogita, Rump
+// and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005, with double-word
+// operands): the running sum of the leading products in one float, every rounding error (the
+// exact error of each leading product, the cross terms, the TwoSum error of each addition)
+// gathered in a second float, and one renormalisation at the end instead of one per term.
+struct ffacc {
+  float s, c;
+};
+__device__ __forceinline__ void ffacc_fma(ffacc& A, ff a, ff b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const ff t = ff_two_sum(A.s, p);
+  A.s = t.h;
+  A.c += t.l + e;
+}
+__device__ __forceinline__ ff ffacc_fin(ffacc A) { return ff_two_sum(A.s, A.c); }
+
 // double -> ff by integer manipulation of the bit pattern (no FP64 instruction): hi keeps the
 // leading 24 significand bits (truncated), lo the next bits of the remainder; exact to 2^-47
 // relative for normal doubles whose exponent lies in [-74, 127]; smaller magnitudes keep hi only.

@@ -575,10 +575,17 @@ __global__ void __launch_bounds__(Sz<DIM, NP>::BT, StageMinBlocks<T>::value) k_s
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const T* ue = su + le2 * EU + v * N;
-        T s = zero_t<T>();
+        if constexpr (std::is_same<T, ff>::value) {
+          ffacc A{0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[pts[j]], s);
-        to[v * NF] = s;
+          for (int j = 0; j < NP; ++j) ffacc_fma(A, lf[j], ue[pts[j]]);
+          to[v * NF] = ffacc_fin(A);
+        } else {
+          T s = zero_t<T>();
+#pragma unroll
+          for (int j = 0; j < NP; ++j) s = fma_t(lf[j], ue[pts[j]], s);
+          to[v * NF] = s;
+        }
       }
     }
   }
