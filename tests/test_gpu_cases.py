@@ -153,6 +153,21 @@ def test_deep_octree_adaptations_unpacked_keys():
     assert o.M > 64
 
 
+def test_large_quadtree_adaptations_without_synchronisation():
+    # 65,536 leaves and more: the unsynchronised balance merge runs more 1024-leaf chunks than its
+    # grid has blocks (two per SM), so its blocks loop over the leaves
+    cfg = _cfg("vortex2d_p2_small", p=1, Dbase=8, Dmax=10, init_passes=0)
+    g = fr.Mesh(cfg)
+    o = O.OracleMesh(cfg)
+    for k in range(3):
+        flags = W.random_flags(o.M, 200 + k, p_refine=0.1, p_coarsen=0.3)
+        g.adapt(flags)
+        o.adapt(flags)
+        assert np.array_equal(g.leaves(), o.leaves())
+        assert rel_l2(g.state(), o.state()) < 1e-12
+    assert o.M > 100_000
+
+
 def test_balance_pass_beyond_octant_capacity():
     # Sixteen stripes across the periodic square, alternately at depth 8 and depth 7 (balanced);
     # refining every depth-8 leaf puts depth-9 leaves against depth-7 ones along all sixteen
