@@ -120,6 +120,28 @@ def test_conn_rejects_unbalanced():
         assert np.array_equal(a, b)
 
 
+def test_balance_of_a_deep_strip_beside_a_coarse_leaf():
+    # one quadrant refined to depth 14 along its right edge, beside a depth-1 leaf: the first
+    # balance pass must split that leaf all the way down along 8192 finest cells, far more octants
+    # than the room of the pass's single search (max(2^16, 2n)), so the pass is counted, scanned
+    # and generated again at exact positions
+    Dmax, X0 = 14, 8192
+    boxes = [(1, 8192, 0, 0), (1, 0, 8192, 0), (1, 8192, 8192, 0)]
+    stack = [(1, 0, 0)]
+    while stack:
+        d, x, y = stack.pop()
+        w = 1 << (Dmax - d)
+        if x + w == X0 and d < Dmax:
+            for c in range(4):
+                stack.append((d + 1, x + (c & 1) * (w // 2), y + (c >> 1) * (w // 2)))
+        else:
+            boxes.append((d, x, y, 0))
+    keys = np.sort(O.morton_encode(2, Dmax, np.array(boxes)))
+    want = O.balance(2, Dmax, keys)
+    assert len(keys) == 24577 and len(want) == 37000
+    assert np.array_equal(fr.tree_balance(2, Dmax, keys), want)
+
+
 def test_large_balance_sampled():
     # a 2D tree of ~10^6 leaves at Dmax 14: compare the whole result (the oracle finishes it)
     _, keys = _tree(2, 6, 14, 99, 0.22, max_leaves=1200000)
