@@ -61,3 +61,22 @@ def test_oracle_timer_rates(monkeypatch, whole):
 def test_host_cpu():
     h = bench.host_cpu()
     assert h["nproc"] == os.cpu_count() and h["model"] and h["machine"]
+
+
+def test_reference_arm_line(capsys, monkeypatch):
+    # `bench.py --impl reference` on the small 2D workload (whole cycles of the oracle): one JSON
+    # line with the reference arm's keys, the same config as the GPU arm's, and no host copies
+    import json
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "vortex2d_p2_small",
+                                      "--steps", "1", "--warmup", "3"])
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(bench, "WORKLOAD", bench.WORKLOAD)
+    assert bench.main() == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["metric"] == bench.METRIC
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 3
+    assert line["config"] == bench._config_line(W.config("vortex2d_p2_small"))
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["value"] > 0 and line["e2e"]["value"] == line["value"]
