@@ -452,7 +452,7 @@ int adapt_impl(fr_mesh* m, const int8_t* d_flags, fr_adapt_stats* st, bool trans
   KeyIndex X;
   bool conn_dirty = false;  // the mesh's connectivity tables now describe the new tree
   // the traces of unchanged elements are carried over by the transfer (when the current ones are
-  // valid); only refined and fused elements get theirs computed afterwards
+  // valid), which also computes those of the refined and fused elements from their new state
   const bool carry = transfer && m->traces_ok;
   // issued without synchronisation, the edit and the balance passes carry each new leaf's origin
   // in the old tree (src) and its relation to it (tag): the old->new mapping of Sec. 4.2 without a
